@@ -1,0 +1,318 @@
+/*
+ * fj.h -- C ABI of libfj.so: Free Join plans executed over COLT indexes on a
+ * GB300 (sm_103a).
+ *
+ * Paper: Wang, Willsey, Suciu, "Free Join: Unifying Worst-Case Optimal and
+ * Traditional Joins" (arXiv 2301.10841).  The library takes what the paper's
+ * entry point takes (Section 5.1): base relations stored column-wise and a
+ * full conjunctive query (Section 2.1, Eq. 1), plus either a left-deep binary
+ * plan to convert (Section 4.1) or a Free Join plan (Def. 3.3).  It builds
+ * COLT levels lazily on the GPU (Section 4.2, Def. 4.1) and runs the plan
+ * with vectorized, batch-at-a-time execution (Section 4.3) and the
+ * fewest-keys dynamic cover (Section 4.4).
+ *
+ * Conventions shared by every call:
+ *   - Values are int32 (signed comparison); row offsets are uint32, so a
+ *     relation holds fewer than 2^32 - 1 rows; counts are uint64.
+ *   - Variable ids are small integers in [0, FJ_MAX_VARS).
+ *   - No call throws.  Every fallible call returns an fj_status; on failure
+ *     fj_last_error() holds a one-line message for the calling thread.
+ *   - "Device pointer" means memory of the context's GPU; "host pointer"
+ *     means ordinary (or pinned) CPU memory.
+ *   - Work is enqueued on the context's CUDA stream.  Calls that return
+ *     results to the host synchronize that stream once before returning.
+ */
+#ifndef FJ_H_
+#define FJ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t fj_status;
+
+#define FJ_OK 0
+#define FJ_ERR_INVALID_ARG (-1)      /* bad pointer, size or id */
+#define FJ_ERR_INVALID_PLAN (-2)     /* violates Def. 3.3 / Def. 3.4 */
+#define FJ_ERR_OOM (-3)              /* device allocation failed */
+#define FJ_ERR_OUTPUT_OVERFLOW (-4)  /* materialized output above list_limit */
+#define FJ_ERR_COUNT_OVERFLOW (-5)   /* COUNT(*) does not fit in uint64 */
+#define FJ_ERR_TIMEOUT (-6)          /* a bounded device wait ran out */
+#define FJ_ERR_CUDA (-7)             /* a CUDA runtime call failed */
+#define FJ_ERR_UNSUPPORTED (-8)      /* a shape this build does not handle */
+
+#define FJ_MAX_VARS 32   /* distinct variables per query */
+#define FJ_MAX_ATOMS 16  /* atoms per query */
+#define FJ_MAX_NODES 16  /* nodes per Free Join plan */
+#define FJ_MAX_SUB 16    /* subatoms per node */
+#define FJ_MAX_ARITY 8   /* variables per atom */
+#define FJ_MAX_PREDS 4   /* pushed-down predicates per atom */
+
+typedef struct fj_ctx fj_ctx;
+typedef struct fj_rel fj_rel;
+typedef struct fj_prepared fj_prepared;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (for example torch.cuda.current_stream().cuda_stream) or NULL for the
+ * legacy default stream; the library enqueues all of its work there and
+ * never synchronizes the device.  The context owns a private stream-ordered
+ * memory pool for COLT levels and intermediate batches.  *out receives the
+ * handle; destroy it with fj_ctx_destroy.  Errors: FJ_ERR_INVALID_ARG,
+ * FJ_ERR_CUDA. */
+fj_status fj_ctx_create(int device, void* cuda_stream, fj_ctx** out);
+
+/* Release every relation, prepared plan and buffer the context owns.  Safe on
+ * NULL. */
+void fj_ctx_destroy(fj_ctx* ctx);
+
+/* Replace the stream work is enqueued on (same device).  FJ_ERR_INVALID_ARG
+ * on a NULL context. */
+fj_status fj_ctx_set_stream(fj_ctx* ctx, void* cuda_stream);
+
+/* Last error message of the calling thread (never NULL; "" after success). */
+const char* fj_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Relations (Section 2.1; Section 4.2: "each column is stored as a vector")  */
+/* ------------------------------------------------------------------------ */
+
+/* Register a column-stored relation whose `n_cols` int32 columns of `n_rows`
+ * values each already live in device memory (`d_cols[j]` a device pointer,
+ * 4-byte aligned).  The pointers are BORROWED: the caller keeps them alive
+ * and unchanged until fj_release_relation; the library never writes or frees
+ * them.  `name` is copied (may be NULL).  Errors: FJ_ERR_INVALID_ARG
+ * (n_cols outside [1, FJ_MAX_ARITY*4], n_rows >= 2^32 - 1, NULL column). */
+fj_status fj_load_relation(fj_ctx* ctx, const char* name, int n_cols,
+                           const int32_t* const* d_cols, uint64_t n_rows,
+                           fj_rel** out);
+
+/* Same, but the columns are HOST pointers: the library allocates device
+ * columns it owns and copies the data on the context's stream (page-locked
+ * host memory makes the copy asynchronous and fastest).  The host buffers may
+ * be reused once the call returns only after the stream is synchronized;
+ * fj_execute_plan synchronizes it.  Errors as fj_load_relation, plus
+ * FJ_ERR_OOM and FJ_ERR_CUDA. */
+fj_status fj_load_relation_host(fj_ctx* ctx, const char* name, int n_cols,
+                                const int32_t* const* h_cols, uint64_t n_rows,
+                                fj_rel** out);
+
+/* Forget a relation (and free its columns if the library owns them).  Any
+ * prepared plan that references it must be freed first.  Safe on NULL. */
+void fj_release_relation(fj_ctx* ctx, fj_rel* rel);
+
+/* Number of rows of a relation (0 on NULL). */
+uint64_t fj_relation_rows(const fj_rel* rel);
+
+/* ------------------------------------------------------------------------ */
+/* Queries and plans (Section 2.1 Eq. 1; Section 3.2 Def. 3.2-3.4)           */
+/* ------------------------------------------------------------------------ */
+
+/* Pushed-down selection on one atom column (Section 2.1: "selections are
+ * pushed down to the base tables"): keep rows with  value(col) OP value. */
+#define FJ_LT 0
+#define FJ_LE 1
+#define FJ_GT 2
+#define FJ_GE 3
+#define FJ_EQ 4
+#define FJ_NE 5
+typedef struct {
+  int col;       /* index j into the atom's vars (0 <= j < n_vars) */
+  int op;        /* FJ_LT .. FJ_NE */
+  int32_t value;
+} fj_pred;
+
+/* An atom R(x1..xk): variable vars[j] is read from column cols[j] of the
+ * relation (cols NULL means column j).  The variables of one atom are
+ * distinct (Section 2.1).  A self-join is two atoms over the same relation;
+ * each atom gets its own COLT (Section 2.1: "we simply rename one"). */
+typedef struct {
+  fj_rel* rel;
+  int n_vars;
+  const int* vars;
+  const int* cols;
+  int n_preds;
+  const fj_pred* preds;
+} fj_atom;
+
+/* Q(head) :- atoms.  The query is full: head_vars lists every variable of the
+ * atoms exactly once, in output column order (NULL head_vars means first
+ * appearance across atoms in order). */
+typedef struct {
+  int n_atoms;
+  const fj_atom* atoms;
+  int n_head;
+  const int* head_vars;
+} fj_query;
+
+/* A subatom R(y) with y a subset of the atom's variables (Def. 3.2).  The
+ * variables may be listed in any order; the library uses the atom's column
+ * order.  n_vars may be 0 (the empty subatom R(), which iterates the leaf
+ * vector, i.e. the multiplicity). */
+typedef struct {
+  int atom;       /* index into fj_query.atoms */
+  int n_vars;
+  const int* vars;
+} fj_subatom;
+
+/* A node phi_k: its subatoms; sub[0] is the designated (static) cover. */
+typedef struct {
+  int n_sub;
+  const fj_subatom* sub;
+} fj_node;
+
+/* A Free Join plan [phi_0 .. phi_{n-1}] (Def. 3.3).  When returned by the
+ * library, every array it points to is owned by the plan and released by
+ * fj_plan_free. */
+typedef struct {
+  int n_nodes;
+  const fj_node* nodes;
+} fj_plan;
+
+/* Check that `plan` partitions every atom of `query` into subatoms
+ * (Def. 3.3) and is valid (Def. 3.4: no two subatoms of one atom in a node;
+ * every node has a cover, i.e. a subatom holding vs(phi_k) - avs(phi_k)),
+ * and that sub[0] of every node is a cover.  Host only.  Returns FJ_OK or
+ * FJ_ERR_INVALID_PLAN / FJ_ERR_INVALID_ARG with the reason in
+ * fj_last_error(). */
+fj_status fj_validate_plan(const fj_query* query, const fj_plan* plan);
+
+/* binary2fj (Section 4.1, Fig. 12): convert the left-deep binary plan
+ * [R_order[0], ..., R_order[n-1]] (atom indices, a permutation of
+ * 0..n_atoms-1) into a Free Join plan; then, if apply_factor != 0, apply
+ * factor (Fig. 13), moving probe subatoms one node earlier while their
+ * variables are available there and the earlier node has no subatom of the
+ * same atom, stopping at the first that cannot move.  Host only.  *out is
+ * library-owned; release with fj_plan_free.  Errors: FJ_ERR_INVALID_ARG. */
+fj_status fj_binary_to_free_plan(const fj_query* query, const int* order,
+                                 int n, int apply_factor, fj_plan** out);
+
+/* Release a plan returned by fj_binary_to_free_plan.  Safe on NULL. */
+void fj_plan_free(fj_plan* plan);
+
+/* GHT schema of atom `atom` under `plan` (Section 3.3, build phase): the
+ * subatoms of the atom in plan order give the levels y0..y(l-1), and an empty
+ * last level is appended unless the last subatom is its node's cover.
+ * Writes into level_sizes[0..*n_levels) the number of variables per level and
+ * into vars_out the variables level by level (capacity FJ_MAX_ARITY*2 and
+ * FJ_MAX_ARITY respectively suffice).  Host only. */
+fj_status fj_ght_schema(const fj_query* query, const fj_plan* plan, int atom,
+                        int* n_levels, int* level_sizes, int* vars_out);
+
+/* Covers of node k (Def. 3.4): writes the indices into node.sub of every
+ * subatom that holds vs(phi_k) - avs(phi_k); *n_covers receives how many
+ * (capacity FJ_MAX_SUB).  Host only. */
+fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
+                         int* n_covers, int* covers_out);
+
+/* ------------------------------------------------------------------------ */
+/* Execution (Section 3.3 Fig. 7; Section 4.2 COLT; Section 4.3 Fig. 11;      */
+/* Section 4.4 dynamic cover)                                                */
+/* ------------------------------------------------------------------------ */
+
+#define FJ_COVER_STATIC 0   /* iterate sub[0] of every node */
+#define FJ_COVER_FEWEST 1   /* per partial tuple, the cover with fewest keys
+                               (an unforced COLT vector counts its length) */
+#define FJ_COVER_LEARNED 2  /* as FEWEST, with keys scaled by a learned model */
+
+#define FJ_OUT_MATERIALIZE 0  /* write every output tuple (bag) */
+#define FJ_OUT_COUNT 1        /* COUNT(*) only */
+#define FJ_OUT_COUNT_MIN 2    /* COUNT(*) and MIN of each min_vars[i] */
+
+#define FJ_FLAG_EAGER_ALL 1u   /* force every COLT level before the join
+                                  ("simple trie", paper Section 5.3) */
+#define FJ_FLAG_EAGER_ROOT 2u  /* force every root level before the join
+                                  ("simple lazy trie", Section 5.3) */
+
+typedef struct {
+  uint32_t batch_size;   /* cover tuples per vectorized batch (Fig. 11);
+                            0 = default 2048; rounded to a supported size */
+  float load_factor;     /* COLT hash-level occupancy target; 0 = 0.5 */
+  int cover_policy;      /* FJ_COVER_* */
+  int out_mode;          /* FJ_OUT_* */
+  uint64_t list_limit;   /* MATERIALIZE: most rows to keep (0 = no limit) */
+  int n_min_vars;        /* COUNT_MIN: variables to take MIN of */
+  const int* min_vars;
+  uint64_t spin_limit;   /* bound on any device-side wait; 0 = default */
+  const void* model;     /* FJ_COVER_LEARNED: an fj_model*; else NULL */
+  uint32_t flags;        /* FJ_FLAG_* */
+} fj_exec_opts;
+
+/* Counter slots of fj_result.counters. */
+#define FJ_CTR_COVER_ITERS 0    /* cover elements iterated, all nodes */
+#define FJ_CTR_PROBES 1         /* hash-level lookups issued */
+#define FJ_CTR_PROBE_HITS 2     /* lookups that found their key */
+#define FJ_CTR_ROOTS_BUILT 3    /* root levels built (atoms indexed) */
+#define FJ_CTR_SUBTRIES_FORCED 4 /* child vectors turned into maps (level>=1) */
+#define FJ_CTR_ROWS_REGROUPED 5 /* offsets moved by forcing, all levels */
+#define FJ_CTR_SURVIVORS 6      /* partial tuples that reached the last node */
+#define FJ_CTR_CHUNKS 7         /* expansion chunks launched */
+#define FJ_CTR_KERNELS 8        /* kernels launched by this execution */
+#define FJ_CTR_ATOM_BUILT_MASK 9  /* bit a set: atom a's root level was built */
+
+typedef struct {
+  uint64_t count;                  /* COUNT(*) over the bag result */
+  int32_t mins[FJ_MAX_VARS];       /* MIN of min_vars[i] (COUNT_MIN) */
+  uint8_t min_valid[FJ_MAX_VARS];  /* 0: empty result (SQL NULL) */
+  int n_head;                      /* columns of d_tuples */
+  uint64_t n_out;                  /* rows in d_tuples */
+  int32_t* d_tuples;               /* MATERIALIZE: device buffer, row-major
+                                      n_out x n_head, head order, unsorted */
+  int tuples_owned;                /* 1: d_tuples belongs to this result
+                                      (fj_execute_plan) and is released by
+                                      fj_result_free; 0: it belongs to the
+                                      prepared plan (fj_execute_prepared) and
+                                      stays valid until its next execution
+                                      or fj_prepared_free */
+  uint64_t counters[16];           /* FJ_CTR_* */
+} fj_result;
+
+/* One-shot execution: build what the plan needs and run it (lazily, from
+ * scratch) and fill *out.  Enqueued on the context's stream; synchronizes it
+ * once at the end to read the status, count and MINs.  `plan` must be valid
+ * for `query` (checked: FJ_ERR_INVALID_PLAN).  Errors: FJ_ERR_INVALID_ARG,
+ * FJ_ERR_INVALID_PLAN, FJ_ERR_OOM, FJ_ERR_OUTPUT_OVERFLOW (more rows than
+ * list_limit; count is still exact and d_tuples holds list_limit rows),
+ * FJ_ERR_COUNT_OVERFLOW, FJ_ERR_TIMEOUT, FJ_ERR_CUDA, FJ_ERR_UNSUPPORTED. */
+fj_status fj_execute_plan(fj_ctx* ctx, const fj_query* query,
+                          const fj_plan* plan, const fj_exec_opts* opts,
+                          fj_result* out);
+
+/* Prepared execution.  fj_prepare validates and compiles the plan once and
+ * allocates COLT storage, with nothing built.  fj_build_colt_level forces
+ * schema level `level` of atom `atom` for every entry of the level above it
+ * (the eager ablations of Section 5.3; level 0 is the root hash map over the
+ * selected base table); it fails with FJ_ERR_UNSUPPORTED for a level the
+ * plan only iterates unless prepared with FJ_FLAG_EAGER_ALL.
+ * fj_execute_prepared runs the join, reusing (and lazily extending) the
+ * levels already built -- COLT is a cache of the base tables.
+ * fj_reset_prepared drops every built level so the next execution starts
+ * from the base tables again.  The query's and plan's arrays are copied;
+ * relations must outlive the prepared plan. */
+fj_status fj_prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* plan,
+                     const fj_exec_opts* opts, fj_prepared** out);
+fj_status fj_build_colt_level(fj_prepared* prep, int atom, int level);
+fj_status fj_execute_prepared(fj_prepared* prep, fj_result* out);
+fj_status fj_reset_prepared(fj_prepared* prep);
+void fj_prepared_free(fj_prepared* prep);
+
+/* Copy a materialized result's rows (n_out x n_head int32) to `dst`, a
+ * device pointer if dst_is_device != 0 else a host pointer.  Synchronizes the
+ * stream.  FJ_ERR_INVALID_ARG if the result holds no tuples. */
+fj_status fj_result_copy_tuples(fj_ctx* ctx, const fj_result* res, void* dst,
+                                int dst_is_device);
+
+/* Release the device buffer of a result (safe to call twice). */
+void fj_result_free(fj_ctx* ctx, fj_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FJ_H_ */

@@ -1,0 +1,947 @@
+// libfj host engine: contexts, relations, plan compilation and the node
+// driver.  All compute runs in the kernels of fj_kernels.cuh / fj_exec.cuh.
+//
+// Execution of a prepared plan (paper Section 3.3 build + join phases, with
+// COLT making the build phase lazy, Section 4.2):
+//   1. reset the per-execution COLT state (nothing is built yet);
+//   2. run node 0 on the single empty partial tuple;
+//   3. for node k: choose a cover per partial tuple and request the COLT
+//      levels it will probe or iterate as a map (k_choose); force exactly
+//      those (the k_force_* sequence, batched over atoms); count each tuple's
+//      cover elements and prefix-sum them (k_fanout + scan); expand the
+//      position space in chunks bounded by the next node's buffer
+//      (k_expand), recursing into node k+1 after every chunk;
+//   4. the last expanded node aggregates (COUNT, MIN, with the remaining
+//      single-vector nodes folded in as product factors) or materializes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fj_exec.cuh"
+#include "fj_plan.h"
+
+using namespace fj;
+
+struct fj_rel {
+  fj_ctx* ctx = nullptr;
+  std::string name;
+  std::vector<const int32_t*> cols;
+  uint64_t n_rows = 0;
+  std::vector<void*> owned;
+};
+
+struct fj_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  int n_sm = 0;
+  ResultDev* d_res = nullptr;
+  ResultDev* h_res = nullptr;   // pinned
+  uint64_t* h_total = nullptr;  // pinned
+  void* d_partials = nullptr;   // scan partials: kMaxScanJobs x kScanBlocks x 8 B
+};
+
+namespace {
+
+constexpr int kMaxScanJobs = FJ_MAX_ATOMS;
+
+struct Error {
+  fj_status st;
+  std::string msg;
+};
+
+[[noreturn]] void fail(fj_status st, const std::string& msg) { throw Error{st, msg}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      fail(FJ_ERR_OOM, std::string(what) + ": out of device memory");
+    }
+    fail(FJ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+#define CK(x) cuda_check((x), #x)
+#define CK_LAUNCH(what) cuda_check(cudaGetLastError(), what)
+
+template <typename T>
+T* dalloc(fj_ctx* c, size_t n) {
+  void* p = nullptr;
+  CK(cudaMallocFromPoolAsync(&p, std::max<size_t>(n, 1) * sizeof(T), c->pool, c->stream));
+  return static_cast<T*>(p);
+}
+
+void dfree(fj_ctx* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+template <typename F>
+fj_status guarded(F&& f) {
+  try {
+    f();
+    set_error("");
+    return FJ_OK;
+  } catch (const Error& e) {
+    set_error(e.msg);
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FJ_ERR_OOM;
+  }
+}
+
+uint32_t pow2_at_least(uint64_t x) {
+  uint64_t c = 16;
+  while (c < x) c <<= 1;
+  if (c > (1ull << 31)) fail(FJ_ERR_UNSUPPORTED, "hash level too large");
+  return uint32_t(c);
+}
+
+int blocks_for(uint64_t work, int per_block, int cap) {
+  uint64_t b = (work + per_block - 1) / per_block;
+  return int(std::max<uint64_t>(1, std::min<uint64_t>(b, uint64_t(cap))));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Prepared plans.
+// ---------------------------------------------------------------------------
+
+struct ItemsBuf {
+  int32_t* var[FJ_MAX_VARS] = {};
+  uint32_t* h[FJ_MAX_ATOMS] = {};
+  uint64_t* mult = nullptr;
+  uint8_t* choice = nullptr;
+  uint64_t* fan = nullptr;
+  uint64_t* scan = nullptr;
+  uint64_t* total = nullptr;
+  uint32_t* n = nullptr;
+  uint32_t cap = 0;
+};
+
+struct AtomPlan {
+  int n_levels = 0;                     // schema levels
+  std::vector<int> level_node;          // node of each schema level
+  std::vector<std::vector<int>> level_vars;
+  std::vector<bool> may_force;          // per L index (1..n_levels)
+};
+
+struct fj_prepared {
+  fj_ctx* ctx = nullptr;
+  PQuery q;
+  PPlan plan;
+  fj_exec_opts opts{};
+  std::vector<int> min_vars;
+  std::vector<fj_rel*> rels;
+  std::vector<AtomPlan> ap;
+  std::vector<AtomDev> host_atoms;
+  AtomDev* d_atoms = nullptr;
+  std::vector<void*> allocs;
+  int n_nodes = 0;
+  int tail_start = 0;  // first node folded into the aggregation epilogue
+  int last = 0;        // last expanded node
+  std::vector<NodeDev> nd;
+  std::vector<ItemsBuf> items;             // items[k]: input of node k
+  std::vector<std::vector<int2>> jobs;     // force jobs per node
+  std::vector<int2*> d_jobs;
+  int2* d_level_jobs = nullptr;            // [atom][level] single jobs
+  std::vector<uint32_t> max_rows_job;      // per node: largest atom among its jobs
+  std::vector<uint32_t> max_req_job;
+  int32_t* d_out = nullptr;
+  uint64_t out_cap = 0;
+  bool materialize = false;
+  size_t smem_expand = 0;
+  int expand_blocks_per_sm = 1;
+  uint64_t kernels = 0;
+  uint64_t chunks = 0;
+
+  template <typename T>
+  T* alloc(size_t n) {
+    T* p = dalloc<T>(ctx, n);
+    allocs.push_back(p);
+    return p;
+  }
+};
+
+namespace {
+
+// Scans ---------------------------------------------------------------------
+
+template <typename T, typename Op>
+void run_scan(fj_prepared* P, Op op, int n_jobs, uint64_t ub_n) {
+  fj_ctx* c = P->ctx;
+  int nb = blocks_for(ub_n, 4096, kScanBlocks);
+  dim3 g(nb, n_jobs);
+  k_scan_reduce<T, Op><<<g, kThreads, 0, c->stream>>>(op, static_cast<T*>(c->d_partials));
+  k_scan_mid<T, Op><<<dim3(1, n_jobs), 1024, 0, c->stream>>>(op, static_cast<T*>(c->d_partials),
+                                                             nb);
+  k_scan_down<T, Op><<<g, kThreads, 0, c->stream>>>(op, static_cast<T*>(c->d_partials));
+  CK_LAUNCH("scan");
+  P->kernels += 3;
+}
+
+// COLT forcing of a batch of (atom, level) jobs.
+void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uint32_t ub_req) {
+  if (n_jobs == 0) return;
+  fj_ctx* c = P->ctx;
+  cudaStream_t s = c->stream;
+  ForceJobs fj{P->d_atoms, d_jobs, n_jobs};
+  int cap = c->n_sm * 8;
+  int g_rows = blocks_for(ub_rows, kThreads * 4, cap);
+  int g_ht = blocks_for(uint64_t(ub_rows) * 2 + 2, kThreads * 4, cap);
+  k_force_count<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
+  k_force_prepare<<<n_jobs, 32, 0, s>>>(fj);
+  k_force_clear<<<dim3(g_ht, n_jobs), kThreads, 0, s>>>(fj);
+  CK_LAUNCH("force prepare");
+  P->kernels += 3;
+  run_scan<uint32_t>(P, RowOffOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
+  k_force_insert<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, c->d_res);
+  CK_LAUNCH("force insert");
+  P->kernels += 1;
+  run_scan<uint32_t>(P, ChildFirstOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
+  k_force_assign<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
+  P->kernels += 1;
+  run_scan<uint32_t>(P, EntryPosOp{P->d_atoms, d_jobs}, n_jobs, ub_rows);
+  k_force_begin<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
+  k_force_scatter<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
+  k_force_finish<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, c->d_res);
+  k_force_reset_req<<<n_jobs, 32, 0, s>>>(fj);
+  CK_LAUNCH("force finish");
+  P->kernels += 5;
+}
+
+void sync_read_total(fj_prepared* P, const uint64_t* d_total, uint64_t* out) {
+  fj_ctx* c = P->ctx;
+  CK(cudaMemcpyAsync(c->h_total, d_total, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = *c->h_total;
+}
+
+void run_node(fj_prepared* P, int k, uint64_t ub_items) {
+  fj_ctx* c = P->ctx;
+  cudaStream_t s = c->stream;
+  NodeDev nd = P->nd[k];
+  int g_items = blocks_for(ub_items, kThreads, c->n_sm * 8);
+  k_choose<<<g_items, kThreads, 0, s>>>(nd, P->d_atoms);
+  CK_LAUNCH("choose");
+  P->kernels += 1;
+  force(P, P->d_jobs[k], int(P->jobs[k].size()), P->max_rows_job[k], P->max_req_job[k]);
+  k_fanout<<<g_items, kThreads, 0, s>>>(nd, P->d_atoms);
+  CK_LAUNCH("fanout");
+  P->kernels += 1;
+  run_scan<uint64_t>(P,
+                     FanScanOp{nd.fan, nd.scan, nd.total, nd.n_items, nd.single_item},
+                     1, ub_items);
+  uint64_t total = 0;
+  sync_read_total(P, nd.total, &total);
+  if (total == 0) return;
+  bool items_mode = nd.mode == kModeItems;
+  uint64_t step = items_mode ? P->items[k + 1].cap : total;
+  for (uint64_t c0 = 0; c0 < total; c0 += step) {
+    nd.chunk_begin = c0;
+    nd.chunk_end = std::min(total, c0 + step);
+    if (items_mode) CK(cudaMemsetAsync(P->items[k + 1].n, 0, sizeof(uint32_t), s));
+    int grid = blocks_for(nd.chunk_end - c0, nd.tile, c->n_sm * P->expand_blocks_per_sm);
+    k_expand<<<grid, kThreads, P->smem_expand, s>>>(nd, P->d_atoms, c->d_res);
+    CK_LAUNCH("expand");
+    P->kernels += 1;
+    P->chunks += 1;
+    if (items_mode) run_node(P, k + 1, nd.chunk_end - c0);
+  }
+}
+
+}  // namespace
+
+// Compile query + plan into device descriptors and allocate COLT storage.
+static void compile(fj_prepared* P) {
+  fj_ctx* c = P->ctx;
+  const PQuery& q = P->q;
+  const PPlan& plan = P->plan;
+  const fj_exec_opts& o = P->opts;
+  int na = int(q.atom_vars.size());
+  int nn = int(plan.size());
+  P->n_nodes = nn;
+  P->materialize = o.out_mode == FJ_OUT_MATERIALIZE;
+  bool dyn_policy = o.cover_policy == FJ_COVER_FEWEST || o.cover_policy == FJ_COVER_LEARNED;
+
+  // Per-atom schema levels and which of them may be forced.
+  P->ap.assign(na, {});
+  std::vector<std::vector<int>> lvl_of(nn);  // per node, per sub: schema level
+  std::vector<std::vector<int>> cov(nn);
+  for (int k = 0; k < nn; ++k) {
+    cov[k] = covers(plan, k);
+    for (const PSub& sa : plan[k]) {
+      AtomPlan& A = P->ap[sa.atom];
+      lvl_of[k].push_back(A.n_levels);
+      A.level_node.push_back(k);
+      A.level_vars.push_back(sa.vars);
+      A.n_levels++;
+    }
+  }
+  for (int a = 0; a < na; ++a) P->ap[a].may_force.assign(P->ap[a].n_levels + 2, false);
+  std::vector<int> dynamic(nn, 0);
+  for (int k = 0; k < nn; ++k) {
+    dynamic[k] = dyn_policy && cov[k].size() > 1;
+    for (int s = 0; s < int(plan[k].size()); ++s) {
+      const PSub& sa = plan[k][s];
+      AtomPlan& A = P->ap[sa.atom];
+      int l = lvl_of[k][s];
+      bool last = l == A.n_levels - 1;
+      bool probed = dynamic[k] ? true : s != 0;
+      bool map_iter = !last;
+      if (probed || map_iter) A.may_force[l + 1] = true;
+    }
+  }
+  if (o.flags & (FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT))
+    for (int a = 0; a < na; ++a) {
+      P->ap[a].may_force[1] = true;
+      if (o.flags & FJ_FLAG_EAGER_ALL)
+        for (int l = 1; l <= P->ap[a].n_levels; ++l) P->ap[a].may_force[l] = true;
+    }
+  // A level can only be forced below an entry of the level above it.
+  for (int a = 0; a < na; ++a)
+    for (int l = P->ap[a].n_levels; l >= 2; --l)
+      if (P->ap[a].may_force[l]) P->ap[a].may_force[l - 1] = true;
+  // Key-arity limits of forced levels.
+  for (int a = 0; a < na; ++a)
+    for (int l = 1; l <= P->ap[a].n_levels; ++l) {
+      if (!P->ap[a].may_force[l]) continue;
+      int nk = int(P->ap[a].level_vars[l - 1].size());
+      if (nk > 3)
+        fail(FJ_ERR_UNSUPPORTED,
+             "a probed (hashed) subatom holds at most 3 variables (atom " + std::to_string(a) +
+                 ")");
+    }
+
+  // Atom device descriptors and COLT storage.
+  float load = o.load_factor > 0.f ? o.load_factor : 0.5f;
+  if (load > 0.9f) load = 0.9f;
+  P->host_atoms.assign(na, AtomDev{});
+  for (int a = 0; a < na; ++a) {
+    fj_rel* r = P->rels[a];
+    AtomDev& D = P->host_atoms[a];
+    const AtomPlan& A = P->ap[a];
+    D.n_rows = uint32_t(r->n_rows);
+    D.n_vars = int(q.atom_vars[a].size());
+    D.load = load;
+    D.n_levels = A.n_levels + 1;
+    if (D.n_levels > kMaxLevels) fail(FJ_ERR_UNSUPPORTED, "too many levels");
+    bool any_force = false;
+    for (int l = 1; l <= A.n_levels; ++l) any_force |= A.may_force[l];
+    uint32_t n = std::max<uint32_t>(D.n_rows, 1);
+    if (any_force) {
+      D.perm = P->alloc<uint32_t>(n);
+      D.tmp_row = P->alloc<uint32_t>(n);
+      D.tmp_slot = P->alloc<uint32_t>(n);
+      D.newslots = P->alloc<uint32_t>(n);
+    }
+    // L[0]: the virtual root entry.
+    LevelDev& R = D.L[0];
+    R.begin = P->alloc<uint32_t>(1);
+    R.count = P->alloc<uint32_t>(1);
+    R.child_state = P->alloc<uint32_t>(1);
+    R.child_first = P->alloc<uint32_t>(1);
+    R.child_nkeys = P->alloc<uint32_t>(1);
+    R.entries_cap = 1;
+    for (int l = 1; l <= A.n_levels; ++l) {
+      LevelDev& L = D.L[l];
+      const auto& lv = A.level_vars[l - 1];
+      L.nk = int(lv.size());
+      for (int j = 0; j < L.nk && j < 3; ++j) {
+        const auto& av = q.atom_vars[a];
+        L.kcol[j] = int(std::find(av.begin(), av.end(), lv[j]) - av.begin());
+      }
+      L.wide = L.nk == 3 || (L.nk == 2 && l > 1);
+      if (!A.may_force[l]) continue;
+      L.entries_cap = n;
+      L.begin = P->alloc<uint32_t>(n);
+      L.count = P->alloc<uint32_t>(n);
+      L.fill = P->alloc<uint32_t>(n);
+      L.key = P->alloc<uint64_t>(n);
+      L.ht_cap_max = pow2_at_least(uint64_t(double(n) / load) + 1);
+      L.ht = P->alloc<uint4>((size_t(L.ht_cap_max) + 1) * (L.wide ? 2 : 1));
+      L.req_cap = D.L[l - 1].entries_cap;
+      L.req = P->alloc<uint32_t>(L.req_cap);
+      L.rowoff = P->alloc<uint32_t>(size_t(L.req_cap) + 1);
+      LevelDev& Pl = D.L[l - 1];
+      if (!Pl.child_state) {
+        Pl.child_state = P->alloc<uint32_t>(Pl.entries_cap);
+        Pl.child_first = P->alloc<uint32_t>(Pl.entries_cap);
+        Pl.child_nkeys = P->alloc<uint32_t>(Pl.entries_cap);
+      }
+    }
+  }
+
+  // Tail detection (aggregate modes): trailing single-subatom nodes that
+  // iterate their atom's last level below the root.
+  P->tail_start = nn;
+  if (!P->materialize) {
+    while (P->tail_start - 1 >= 1) {
+      int k = P->tail_start - 1;
+      const PSub& sa = plan[k][0];
+      int l = lvl_of[k][0];
+      bool eligible = plan[k].size() == 1 && l == P->ap[sa.atom].n_levels - 1 && l >= 1;
+      if (!eligible) break;
+      P->tail_start--;
+    }
+  }
+  P->last = P->tail_start - 1;
+
+  // Live variables and handles per node input.
+  uint64_t outvars = 0;
+  if (P->materialize)
+    for (int v : q.head) outvars |= 1ull << v;
+  else
+    for (int v : P->min_vars) outvars |= 1ull << v;
+  std::vector<uint64_t> live_in(nn + 1, 0);
+  std::vector<uint32_t> hand_in(nn + 1, 0);
+  for (int k = 0; k <= P->last; ++k) {
+    uint64_t need = outvars;
+    for (int j = k; j <= P->last; ++j) need |= vs_mask(plan[j]);
+    live_in[k] = avs_mask(plan, k) & need;
+    for (int a = 0; a < na; ++a) {
+      int consumed = 0;
+      for (int j = 0; j < k; ++j)
+        for (const PSub& sa : plan[j]) consumed += sa.atom == a;
+      if (consumed >= 1 && consumed < P->ap[a].n_levels) hand_in[k] |= 1u << a;
+    }
+  }
+
+  // Batch tile and shared memory.
+  uint32_t tile = o.batch_size ? o.batch_size : 2048;
+  uint32_t t2 = 256;
+  while (t2 < tile && t2 < 4096) t2 <<= 1;
+  tile = t2;
+  int max_sub = 1;
+  for (int k = 0; k < nn; ++k) max_sub = std::max<int>(max_sub, int(plan[k].size()));
+  auto smem_for = [&](uint32_t t) {
+    return size_t(t) * (8 + 4 + 4 + 4 * max_sub + 2 + 2);
+  };
+  while (tile > 256 && smem_for(tile) > 160 * 1024) tile >>= 1;
+  P->smem_expand = smem_for(tile);
+  CK(cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          int(P->smem_expand)));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P->expand_blocks_per_sm, k_expand, kThreads,
+                                                   P->smem_expand));
+  if (P->expand_blocks_per_sm < 1) P->expand_blocks_per_sm = 1;
+
+  // Item buffers.
+  uint64_t max_rows = 1;
+  for (fj_rel* r : P->rels) max_rows = std::max<uint64_t>(max_rows, r->n_rows);
+  uint32_t cap = uint32_t(std::min<uint64_t>(1ull << 24, std::max<uint64_t>(1ull << 16, max_rows)));
+  P->items.assign(nn + 1, ItemsBuf{});
+  for (int k = 0; k <= P->last; ++k) {
+    ItemsBuf& B = P->items[k];
+    uint32_t bc = k == 0 ? 1u : cap;
+    B.cap = bc;
+    if (k > 0) {
+      for (int v = 0; v < FJ_MAX_VARS; ++v)
+        if (live_in[k] >> v & 1) B.var[v] = P->alloc<int32_t>(bc);
+      for (int a = 0; a < na; ++a)
+        if (hand_in[k] >> a & 1) B.h[a] = P->alloc<uint32_t>(bc);
+      B.mult = P->alloc<uint64_t>(bc);
+    }
+    B.choice = P->alloc<uint8_t>(bc);
+    B.fan = P->alloc<uint64_t>(bc);
+    B.scan = P->alloc<uint64_t>(size_t(bc) + 1);
+    B.total = P->alloc<uint64_t>(1);
+    B.n = P->alloc<uint32_t>(1);
+  }
+
+  // One force job per (atom, level), for explicit builds.
+  {
+    std::vector<int2> all(size_t(na) * kMaxLevels);
+    for (int a = 0; a < na; ++a)
+      for (int l = 0; l < kMaxLevels; ++l) all[size_t(a) * kMaxLevels + l] = make_int2(a, l);
+    P->d_level_jobs = P->alloc<int2>(all.size());
+    CK(cudaMemcpyAsync(P->d_level_jobs, all.data(), sizeof(int2) * all.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  // Node descriptors and force jobs.
+  P->nd.assign(nn, NodeDev{});
+  P->jobs.assign(nn, {});
+  P->d_jobs.assign(nn, nullptr);
+  P->max_rows_job.assign(nn, 1);
+  P->max_req_job.assign(nn, 1);
+  for (int k = 0; k <= P->last; ++k) {
+    NodeDev& N = P->nd[k];
+    std::memset(&N, 0, sizeof(N));
+    N.n_sub = int(plan[k].size());
+    N.dynamic = dynamic[k];
+    N.tile = int(tile);
+    std::memset(N.vpos, -1, sizeof(N.vpos));
+    for (int s = 0; s < N.n_sub; ++s) {
+      const PSub& sa = plan[k][s];
+      SubDev& S = N.sub[s];
+      S.atom = sa.atom;
+      S.lvl = lvl_of[k][s];
+      S.last = S.lvl == P->ap[sa.atom].n_levels - 1;
+      S.nv = int(sa.vars.size());
+      for (int j = 0; j < S.nv; ++j) {
+        S.var[j] = sa.vars[j];
+        const auto& av = q.atom_vars[sa.atom];
+        S.col[j] = int(std::find(av.begin(), av.end(), sa.vars[j]) - av.begin());
+        N.vpos[s][sa.vars[j]] = int8_t(j);
+      }
+      S.hslot = S.lvl >= 1 ? sa.atom : -1;
+      S.bound_mask = 0;
+      for (int j = 0; j < S.nv; ++j)
+        if (avs_mask(plan, k) >> sa.vars[j] & 1) S.bound_mask |= 1u << j;
+      S.is_cover = std::find(cov[k].begin(), cov[k].end(), s) != cov[k].end();
+      if (P->ap[sa.atom].may_force[S.lvl + 1] && (dynamic[k] || s != 0 || !S.last)) {
+        P->jobs[k].push_back(make_int2(sa.atom, S.lvl + 1));
+        P->max_rows_job[k] = std::max<uint32_t>(P->max_rows_job[k], P->host_atoms[sa.atom].n_rows);
+        P->max_req_job[k] =
+            std::max<uint32_t>(P->max_req_job[k], P->host_atoms[sa.atom].L[S.lvl].entries_cap);
+      }
+    }
+    N.avs_mask = uint32_t(avs_mask(plan, k));
+    const ItemsBuf& In = P->items[k];
+    for (int v = 0; v < FJ_MAX_VARS; ++v) N.in_var[v] = In.var[v];
+    for (int a = 0; a < na; ++a) N.in_h[a] = In.h[a];
+    N.in_mult = k == 0 ? nullptr : In.mult;
+    N.choice = In.choice;
+    N.n_items = In.n;
+    N.single_item = k == 0;
+    N.fan = In.fan;
+    N.scan = In.scan;
+    N.total = In.total;
+    N.track_mult = 1;
+    auto touching = [&](int a) {
+      for (int s = 0; s < N.n_sub; ++s)
+        if (plan[k][s].atom == a) return s;
+      return -1;
+    };
+    if (k < P->last) {
+      N.mode = kModeItems;
+      const ItemsBuf& Out = P->items[k + 1];
+      for (int v = 0; v < FJ_MAX_VARS; ++v)
+        if (Out.var[v]) {
+          N.out_var_id[N.n_out_vars] = v;
+          N.out_var[N.n_out_vars] = Out.var[v];
+          N.n_out_vars++;
+        }
+      for (int a = 0; a < na; ++a) {
+        N.out_h[a] = Out.h[a];
+        N.out_h_src[a] = touching(a);
+      }
+      N.out_mult = Out.mult;
+      N.out_n = Out.n;
+      N.out_cap = Out.cap;
+    } else if (!P->materialize) {
+      N.mode = kModeAggregate;
+      uint64_t bound = avs_mask(plan, k) | vs_mask(plan[k]);
+      for (int i = 0; i < int(P->min_vars.size()); ++i) {
+        int v = P->min_vars[i];
+        if (bound >> v & 1) {
+          N.min_var[N.n_min] = v;
+          N.min_idx[N.n_min] = i;
+          N.n_min++;
+        }
+      }
+      for (int t = P->tail_start; t < nn; ++t) {
+        const PSub& sa = plan[t][0];
+        TailDev& T = N.tail[N.n_tail++];
+        T.atom = sa.atom;
+        T.lvl = lvl_of[t][0];
+        T.hsrc = touching(sa.atom);
+        for (int i = 0; i < int(P->min_vars.size()); ++i) {
+          int v = P->min_vars[i];
+          auto it = std::find(sa.vars.begin(), sa.vars.end(), v);
+          if (it == sa.vars.end()) continue;
+          const auto& av = q.atom_vars[sa.atom];
+          T.min_idx[T.n_min] = i;
+          T.min_col[T.n_min] = int(std::find(av.begin(), av.end(), v) - av.begin());
+          T.n_min++;
+        }
+      }
+    } else {
+      N.mode = kModeMaterialize;
+      N.n_head = int(q.head.size());
+      for (int h = 0; h < N.n_head; ++h) N.head_var[h] = q.head[h];
+    }
+    if (!P->jobs[k].empty()) {
+      P->d_jobs[k] = P->alloc<int2>(P->jobs[k].size());
+      CK(cudaMemcpyAsync(P->d_jobs[k], P->jobs[k].data(), sizeof(int2) * P->jobs[k].size(),
+                         cudaMemcpyHostToDevice, c->stream));
+    }
+  }
+}
+
+static void upload_atoms(fj_prepared* P, const fj_query* query) {
+  fj_ctx* c = P->ctx;
+  int na = int(P->q.atom_vars.size());
+  for (int a = 0; a < na; ++a) {
+    AtomDev& D = P->host_atoms[a];
+    const fj_atom& fa = query->atoms[a];
+    fj_rel* r = P->rels[a];
+    for (int j = 0; j < fa.n_vars; ++j) {
+      int col = fa.cols ? fa.cols[j] : j;
+      if (col < 0 || col >= int(r->cols.size()))
+        fail(FJ_ERR_INVALID_ARG, "atom " + std::to_string(a) + ": column index out of range");
+      D.cols[j] = r->cols[col];
+    }
+    D.n_preds = fa.n_preds;
+    for (int p = 0; p < fa.n_preds; ++p) {
+      D.pred_col[p] = fa.preds[p].col;
+      D.pred_op[p] = fa.preds[p].op;
+      D.pred_val[p] = fa.preds[p].value;
+    }
+  }
+  P->d_atoms = P->alloc<AtomDev>(na);
+  CK(cudaMemcpyAsync(P->d_atoms, P->host_atoms.data(), sizeof(AtomDev) * na,
+                     cudaMemcpyHostToDevice, c->stream));
+}
+
+static void ensure_output(fj_prepared* P, uint64_t rows) {
+  if (!P->materialize) return;
+  int nh = int(P->q.head.size());
+  if (P->d_out && P->out_cap >= rows) return;
+  if (P->d_out) dfree(P->ctx, P->d_out);
+  P->out_cap = std::max<uint64_t>(rows, 1);
+  P->d_out = dalloc<int32_t>(P->ctx, size_t(P->out_cap) * nh);
+  P->nd[P->last].out_tuples = P->d_out;
+  P->nd[P->last].out_rows_cap = P->out_cap;
+}
+
+// Reset the COLT state (every level unbuilt) and/or the result accumulators.
+static void reset_state(fj_prepared* P, bool atoms) {
+  fj_ctx* c = P->ctx;
+  int na = int(P->q.atom_vars.size());
+  k_reset<<<na, 32, 0, c->stream>>>(P->d_atoms, na, c->d_res, atoms ? 1 : 0);
+  CK_LAUNCH("reset");
+  P->kernels += 1;
+}
+
+// Force level l (L index, >= 1) of an atom for every entry of the level above.
+static void build_level(fj_prepared* P, int atom, int l) {
+  fj_ctx* c = P->ctx;
+  k_request_all<<<blocks_for(P->host_atoms[atom].L[l - 1].entries_cap, kThreads, c->n_sm * 4),
+                  kThreads, 0, c->stream>>>(P->d_atoms, atom, l);
+  CK_LAUNCH("request_all");
+  P->kernels += 1;
+  force(P, P->d_level_jobs + size_t(atom) * kMaxLevels + l, 1, P->host_atoms[atom].n_rows,
+        P->host_atoms[atom].L[l - 1].entries_cap);
+}
+
+static void eager_builds(fj_prepared* P) {
+  uint32_t fl = P->opts.flags;
+  if (!(fl & (FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT))) return;
+  int na = int(P->q.atom_vars.size());
+  int max_l = 1;
+  if (fl & FJ_FLAG_EAGER_ALL)
+    for (int a = 0; a < na; ++a) max_l = std::max(max_l, P->ap[a].n_levels);
+  for (int l = 1; l <= max_l; ++l)
+    for (int a = 0; a < na; ++a)
+      if (l <= P->ap[a].n_levels) build_level(P, a, l);
+}
+
+static void run_once(fj_prepared* P) {
+  eager_builds(P);
+  run_node(P, 0, 1);
+}
+
+static void read_result(fj_prepared* P, fj_result* out, bool* retry) {
+  fj_ctx* c = P->ctx;
+  CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const ResultDev& r = *c->h_res;
+  *retry = false;
+  if (r.status & kStTableFull) fail(FJ_ERR_CUDA, "internal: COLT hash level overfilled");
+  if (r.status & kStItemsOverflow) fail(FJ_ERR_CUDA, "internal: partial-tuple buffer overflow");
+  if (r.status & kStCountOverflow) fail(FJ_ERR_COUNT_OVERFLOW, "COUNT(*) exceeds 2^64 - 1");
+  std::memset(out, 0, sizeof(*out));
+  out->n_head = int(P->q.head.size());
+  if (P->materialize) {
+    out->count = r.n_out;
+    uint64_t lim = P->opts.list_limit;
+    if (r.status & kStOutputOverflow) {
+      if (lim == 0 || P->out_cap < lim) {
+        *retry = true;  // grow the buffer to the exact size and run again
+        return;
+      }
+    }
+    out->n_out = std::min<uint64_t>(r.n_out, P->out_cap);
+    out->d_tuples = P->d_out;
+    out->tuples_owned = 0;
+  } else {
+    out->count = r.count;
+    for (int i = 0; i < int(P->min_vars.size()); ++i) {
+      out->mins[i] = r.mins[i];
+      out->min_valid[i] = r.count > 0;
+    }
+  }
+  for (int i = 0; i < 16; ++i) out->counters[i] = r.ctr[i];
+  out->counters[FJ_CTR_CHUNKS] = P->chunks;
+  out->counters[FJ_CTR_KERNELS] = P->kernels;
+}
+
+static void execute(fj_prepared* P, fj_result* out) {
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    P->kernels = 0;
+    P->chunks = 0;
+    if (P->materialize) {
+      uint64_t want = P->opts.list_limit ? P->opts.list_limit : (P->out_cap ? P->out_cap : 1u << 20);
+      ensure_output(P, want);
+    }
+    reset_state(P, false);
+    run_once(P);
+    bool retry = false;
+    read_result(P, out, &retry);
+    if (!retry) {
+      if (P->materialize && P->opts.list_limit && out->count > P->opts.list_limit)
+        fail(FJ_ERR_OUTPUT_OVERFLOW, "more output rows than list_limit");
+      return;
+    }
+    uint64_t need = P->ctx->h_res->n_out;
+    if (P->opts.list_limit) need = std::min<uint64_t>(need, P->opts.list_limit);
+    ensure_output(P, need);
+  }
+  fail(FJ_ERR_CUDA, "internal: output sizing did not converge");
+}
+
+static void prepared_release(fj_prepared* P) {
+  if (!P) return;
+  for (void* p : P->allocs) dfree(P->ctx, p);
+  if (P->d_out) dfree(P->ctx, P->d_out);
+  cudaStreamSynchronize(P->ctx->stream);
+  delete P;
+}
+
+static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* plan,
+                            const fj_exec_opts* opts) {
+  if (!ctx) fail(FJ_ERR_INVALID_ARG, "NULL context");
+  std::unique_ptr<fj_prepared> P(new fj_prepared());
+  P->ctx = ctx;
+  if (!load_query(query, P->q)) fail(FJ_ERR_INVALID_ARG, get_error());
+  if (!load_plan(P->q, plan, P->plan)) fail(FJ_ERR_INVALID_PLAN, get_error());
+  if (!validate(P->q, P->plan)) fail(FJ_ERR_INVALID_PLAN, get_error());
+  if (opts) P->opts = *opts;
+  if (P->opts.out_mode < FJ_OUT_MATERIALIZE || P->opts.out_mode > FJ_OUT_COUNT_MIN)
+    fail(FJ_ERR_INVALID_ARG, "bad out_mode");
+  if (P->opts.cover_policy < FJ_COVER_STATIC || P->opts.cover_policy > FJ_COVER_LEARNED)
+    fail(FJ_ERR_INVALID_ARG, "bad cover_policy");
+  if (P->opts.out_mode == FJ_OUT_COUNT_MIN) {
+    if (P->opts.n_min_vars < 0 || P->opts.n_min_vars > FJ_MAX_VARS ||
+        (P->opts.n_min_vars && !P->opts.min_vars))
+      fail(FJ_ERR_INVALID_ARG, "bad min_vars");
+    for (int i = 0; i < P->opts.n_min_vars; ++i) {
+      int v = P->opts.min_vars[i];
+      if (std::find(P->q.head.begin(), P->q.head.end(), v) == P->q.head.end())
+        fail(FJ_ERR_INVALID_ARG, "min variable not in the query");
+      P->min_vars.push_back(v);
+    }
+  }
+  P->opts.min_vars = nullptr;
+  for (int a = 0; a < query->n_atoms; ++a) {
+    fj_rel* r = query->atoms[a].rel;
+    if (!r || r->ctx != ctx) fail(FJ_ERR_INVALID_ARG, "atom without a relation of this context");
+    if (r->n_rows >= 0xffffffffull) fail(FJ_ERR_INVALID_ARG, "relation too large");
+    P->rels.push_back(r);
+  }
+  CK(cudaSetDevice(ctx->device));
+  try {
+    compile(P.get());
+    upload_atoms(P.get(), query);
+    reset_state(P.get(), true);
+  } catch (...) {
+    for (void* p : P->allocs) dfree(ctx, p);
+    throw;
+  }
+  return P.release();
+}
+
+// ---------------------------------------------------------------------------
+// C ABI.
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+fj_status fj_ctx_create(int device, void* cuda_stream, fj_ctx** out) {
+  return guarded([&] {
+    if (!out) fail(FJ_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) fail(FJ_ERR_INVALID_ARG, "no such CUDA device");
+    CK(cudaSetDevice(device));
+    auto* c = new fj_ctx();
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device));
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    CK(cudaMemPoolCreate(&c->pool, &props));
+    uint64_t keep = ~0ull;
+    CK(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    CK(cudaMallocHost(&c->h_res, sizeof(ResultDev)));
+    CK(cudaMallocHost(&c->h_total, sizeof(uint64_t)));
+    c->d_res = dalloc<ResultDev>(c, 1);
+    c->d_partials = dalloc<uint64_t>(c, size_t(kMaxScanJobs) * kScanBlocks);
+    CK(cudaStreamSynchronize(c->stream));
+    *out = c;
+  });
+}
+
+void fj_ctx_destroy(fj_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  dfree(c, c->d_res);
+  dfree(c, c->d_partials);
+  cudaStreamSynchronize(c->stream);
+  if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_total) cudaFreeHost(c->h_total);
+  if (c->pool) cudaMemPoolDestroy(c->pool);
+  delete c;
+}
+
+fj_status fj_ctx_set_stream(fj_ctx* c, void* cuda_stream) {
+  return guarded([&] {
+    if (!c) fail(FJ_ERR_INVALID_ARG, "NULL context");
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  });
+}
+
+fj_status fj_load_relation(fj_ctx* c, const char* name, int n_cols, const int32_t* const* d_cols,
+                           uint64_t n_rows, fj_rel** out) {
+  return guarded([&] {
+    if (!c || !out || !d_cols || n_cols < 1 || n_cols > FJ_MAX_ARITY * 4)
+      fail(FJ_ERR_INVALID_ARG, "fj_load_relation: bad argument");
+    if (n_rows >= 0xffffffffull) fail(FJ_ERR_INVALID_ARG, "fj_load_relation: too many rows");
+    auto* r = new fj_rel();
+    r->ctx = c;
+    r->name = name ? name : "";
+    r->n_rows = n_rows;
+    for (int j = 0; j < n_cols; ++j) {
+      if (!d_cols[j] && n_rows) {
+        delete r;
+        fail(FJ_ERR_INVALID_ARG, "fj_load_relation: NULL column");
+      }
+      r->cols.push_back(d_cols[j]);
+    }
+    *out = r;
+  });
+}
+
+fj_status fj_load_relation_host(fj_ctx* c, const char* name, int n_cols,
+                                const int32_t* const* h_cols, uint64_t n_rows, fj_rel** out) {
+  return guarded([&] {
+    if (!c || !out || !h_cols || n_cols < 1 || n_cols > FJ_MAX_ARITY * 4)
+      fail(FJ_ERR_INVALID_ARG, "fj_load_relation_host: bad argument");
+    if (n_rows >= 0xffffffffull) fail(FJ_ERR_INVALID_ARG, "fj_load_relation_host: too many rows");
+    std::unique_ptr<fj_rel> r(new fj_rel());
+    r->ctx = c;
+    r->name = name ? name : "";
+    r->n_rows = n_rows;
+    try {
+      for (int j = 0; j < n_cols; ++j) {
+        if (!h_cols[j] && n_rows) fail(FJ_ERR_INVALID_ARG, "fj_load_relation_host: NULL column");
+        int32_t* d = dalloc<int32_t>(c, n_rows);
+        r->owned.push_back(d);
+        r->cols.push_back(d);
+        if (n_rows)
+          CK(cudaMemcpyAsync(d, h_cols[j], n_rows * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             c->stream));
+      }
+    } catch (...) {
+      for (void* p : r->owned) dfree(c, p);
+      throw;
+    }
+    *out = r.release();
+  });
+}
+
+void fj_release_relation(fj_ctx* c, fj_rel* r) {
+  if (!r) return;
+  for (void* p : r->owned) dfree(c ? c : r->ctx, p);
+  delete r;
+}
+
+uint64_t fj_relation_rows(const fj_rel* r) { return r ? r->n_rows : 0; }
+
+fj_status fj_prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* plan,
+                     const fj_exec_opts* opts, fj_prepared** out) {
+  return guarded([&] {
+    if (!out) fail(FJ_ERR_INVALID_ARG, "out is NULL");
+    *out = prepare(ctx, query, plan, opts);
+  });
+}
+
+fj_status fj_build_colt_level(fj_prepared* P, int atom, int level) {
+  return guarded([&] {
+    if (!P || atom < 0 || atom >= int(P->q.atom_vars.size()) || level < 0 ||
+        level >= P->ap[atom].n_levels)
+      fail(FJ_ERR_INVALID_ARG, "fj_build_colt_level: bad atom or level");
+    int l = level + 1;
+    if (!P->ap[atom].may_force[l])
+      fail(FJ_ERR_UNSUPPORTED,
+           "fj_build_colt_level: this level is only iterated under the plan and opts; prepare "
+           "with FJ_FLAG_EAGER_ALL to build every level");
+    build_level(P, atom, l);
+  });
+}
+
+fj_status fj_execute_prepared(fj_prepared* P, fj_result* out) {
+  return guarded([&] {
+    if (!P || !out) fail(FJ_ERR_INVALID_ARG, "NULL argument");
+    execute(P, out);
+  });
+}
+
+fj_status fj_reset_prepared(fj_prepared* P) {
+  return guarded([&] {
+    if (!P) fail(FJ_ERR_INVALID_ARG, "NULL prepared plan");
+    reset_state(P, true);
+  });
+}
+
+void fj_prepared_free(fj_prepared* P) { prepared_release(P); }
+
+fj_status fj_execute_plan(fj_ctx* ctx, const fj_query* query, const fj_plan* plan,
+                          const fj_exec_opts* opts, fj_result* out) {
+  fj_prepared* P = nullptr;
+  fj_status st = guarded([&] {
+    if (!out) fail(FJ_ERR_INVALID_ARG, "out is NULL");
+    P = prepare(ctx, query, plan, opts);
+    execute(P, out);
+    if (out->d_tuples) {
+      // Hand the output buffer to the result.
+      P->d_out = nullptr;
+      out->tuples_owned = 1;
+    }
+  });
+  if (P) prepared_release(P);
+  if (st != FJ_OK) set_error(get_error());
+  return st;
+}
+
+fj_status fj_result_copy_tuples(fj_ctx* c, const fj_result* res, void* dst, int dst_is_device) {
+  return guarded([&] {
+    if (!c || !res || !dst || !res->d_tuples) fail(FJ_ERR_INVALID_ARG, "no tuples to copy");
+    size_t bytes = size_t(res->n_out) * res->n_head * sizeof(int32_t);
+    if (bytes)
+      CK(cudaMemcpyAsync(dst, res->d_tuples, bytes,
+                         dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  });
+}
+
+void fj_result_free(fj_ctx* c, fj_result* res) {
+  if (!c || !res || !res->d_tuples) return;
+  if (res->tuples_owned) dfree(c, res->d_tuples);
+  res->d_tuples = nullptr;
+  res->tuples_owned = 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Internal device-side structures of libfj (shared by the host driver and the
+// kernels).  Not part of the public ABI.
+//
+// COLT layout in HBM (paper Section 4.2, Def. 4.1 and Fig. 10).  For every
+// atom the library keeps one array of row offsets `perm` and a stack of levels
+// L[0..n_levels).  L[0] is a virtual level with a single entry standing for
+// the whole relation; L[i] (i >= 1) holds the hash-map nodes of schema level
+// i-1.  An entry e of L[i] is one key of one map node: it owns the contiguous
+// offsets perm[begin[e] .. begin[e]+count[e]) -- the COLT child vector -- and,
+// once that vector is forced into a map of L[i+1], the contiguous entries
+// child_first[e] .. child_first[e]+child_nkeys[e].  Forcing regroups the
+// parent's offsets in place, so a child vector is always a sub-range of its
+// parent's range.  A level's hash table maps the pair (parent entry, key
+// tuple) to the entry, so all map nodes of one level share one table.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/fj.h"
+
+namespace fj {
+
+constexpr int kMaxLevels = FJ_MAX_NODES + 1;  // virtual root + schema levels
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr uint32_t kNone = 0xffffffffu;
+
+// Child-state of an entry: has its child vector been turned into a map?
+constexpr uint32_t kUnforced = 0;
+constexpr uint32_t kRequested = 1;
+constexpr uint32_t kForced = 2;
+
+// Status bits set on the device.
+constexpr uint32_t kStOutputOverflow = 1u << 0;
+constexpr uint32_t kStCountOverflow = 1u << 1;
+constexpr uint32_t kStTableFull = 1u << 2;
+constexpr uint32_t kStItemsOverflow = 1u << 3;
+constexpr uint32_t kStTimeout = 1u << 4;
+
+struct LevelDev {
+  // Entries of this level.
+  uint32_t* begin = nullptr;
+  uint32_t* count = nullptr;
+  uint32_t* fill = nullptr;
+  uint64_t* key = nullptr;
+  uint32_t* child_state = nullptr;
+  uint32_t* child_first = nullptr;
+  uint32_t* child_nkeys = nullptr;
+  uint32_t entries_cap = 0;
+  // Hash table (level >= 1): (cap + 1) 16-byte slots {key lo, key hi, entry,
+  // count}; slot `cap` is reserved for the one key equal to kEmptyKey.
+  uint4* ht = nullptr;
+  uint32_t ht_cap_max = 0;
+  // Key columns: indices into AtomDev::cols (0 to 3 of them).
+  int nk = 0;
+  int kcol[3] = {0, 0, 0};
+  // Wide levels (more than one key value below the root, or three values)
+  // use 32-byte slots {parent, k0, k1, k2 | entry, count, -, -} claimed with
+  // a 16-byte compare-and-swap; their entries keep only the parent in key[]
+  // and read key values from a representative row.
+  int wide = 0;
+  // Forcing work list: parents of L[i-1] whose child vectors must become
+  // maps of this level, and their row-offset prefix sums.
+  uint32_t* req = nullptr;
+  uint32_t* rowoff = nullptr;  // n_req + 1 entries
+  uint32_t req_cap = 0;
+  // Device-side counters (written by kernels).
+  uint32_t mask;       // ht capacity - 1 once cleared
+  uint32_t cleared;    // table cleared for this execution
+  uint32_t n_entries;  // entries created so far
+  uint32_t n_req;      // parents requested in the current force
+  uint32_t n_new;      // entries created by the current force
+  uint32_t n_rows;     // offsets regrouped by the current force
+  uint32_t base;       // first entry id of the current force
+  uint32_t pos_total;  // offsets placed by the current force
+  uint32_t n_in;       // rows that reach this level's table (sizing)
+};
+
+struct AtomDev {
+  const int32_t* cols[FJ_MAX_ARITY];  // column of the atom's j-th variable
+  uint32_t n_rows;
+  int n_vars;
+  int n_preds;
+  int pred_col[FJ_MAX_PREDS];
+  int pred_op[FJ_MAX_PREDS];
+  int32_t pred_val[FJ_MAX_PREDS];
+  uint32_t* perm;      // row offsets, grouped level by level
+  uint32_t* tmp_row;   // per forced row: its offset
+  uint32_t* tmp_slot;  // per forced row: its hash slot
+  uint32_t* newslots;  // slots claimed by the current force
+  uint32_t root_mat;   // perm[0..n_pass) holds the passing rows
+  uint32_t n_pass;
+  float load;
+  int n_levels;
+  LevelDev L[kMaxLevels];
+};
+
+// One subatom of a node, as the expansion kernel sees it.
+struct SubDev {
+  int atom;
+  int lvl;        // level index of the parent handle; entries live in L[lvl+1]
+  int last;       // this subatom is its atom's last schema level
+  int nv;
+  int var[FJ_MAX_ARITY];
+  int col[FJ_MAX_ARITY];  // index into AtomDev::cols per variable
+  int hslot;      // input handle array of this atom (-1: root, handle 0)
+  int is_cover;   // cover candidate of its node
+  uint32_t bound_mask;  // bit j: var[j] was bound by an earlier node; when
+                        // this subatom is iterated as the cover its elements
+                        // must agree with those values
+};
+
+// A tail node: a single-subatom node that iterates the last level of its
+// atom after the last expanded node.  In aggregate modes it contributes the
+// length of its vector as a product factor and the MIN of its variables.
+struct TailDev {
+  int atom;
+  int lvl;   // the vector is the range of the handle's entry in L[lvl]
+  int hsrc;  // >= 0: the new handle of that subatom; -1: the input handle
+  int n_min;
+  int min_idx[FJ_MAX_ARITY];  // index into the result MIN array
+  int min_col[FJ_MAX_ARITY];  // column index into AtomDev::cols
+};
+
+constexpr int kModeItems = 0;
+constexpr int kModeAggregate = 1;
+constexpr int kModeMaterialize = 2;
+
+struct NodeDev {
+  int n_sub;
+  int dynamic;
+  int tile;                               // cover elements per batch
+  SubDev sub[FJ_MAX_SUB];
+  int8_t vpos[FJ_MAX_SUB][FJ_MAX_VARS];   // position of a variable in sub s
+  uint32_t avs_mask;                      // bit v: variable v bound before
+  // Input partial tuples (structure of arrays).
+  const int32_t* in_var[FJ_MAX_VARS];     // by variable id
+  const uint32_t* in_h[FJ_MAX_ATOMS];     // by atom
+  const uint64_t* in_mult;                // null: all 1
+  uint8_t* choice;                        // cover choice per item
+  const uint32_t* n_items;                // device count of input items
+  uint32_t single_item;                   // the input is the one root item
+  uint64_t* fan;                          // per item fanout
+  uint64_t* scan;                         // exclusive fanout prefix (n+1)
+  uint64_t* total;                        // scan[n] copy for the host
+  uint64_t chunk_begin;
+  uint64_t chunk_end;
+  int mode;
+  int track_mult;                         // some probe ends an atom at a leaf
+  // kModeItems.
+  int n_out_vars;
+  int out_var_id[FJ_MAX_VARS];
+  int32_t* out_var[FJ_MAX_VARS];
+  uint32_t* out_h[FJ_MAX_ATOMS];          // by atom; null: not carried
+  int out_h_src[FJ_MAX_ATOMS];            // >= 0: sub index; -1: pass input
+  uint64_t* out_mult;
+  uint32_t* out_n;
+  uint32_t out_cap;
+  // kModeAggregate.
+  int n_tail;
+  TailDev tail[FJ_MAX_NODES];
+  int n_min;
+  int min_var[FJ_MAX_VARS];
+  int min_idx[FJ_MAX_VARS];
+  // kModeMaterialize.
+  int n_head;
+  int head_var[FJ_MAX_VARS];
+  int32_t* out_tuples;
+  uint64_t out_rows_cap;
+};
+
+struct ResultDev {
+  unsigned long long count;
+  int32_t mins[FJ_MAX_VARS];
+  unsigned long long n_out;
+  uint32_t status;
+  uint32_t pad;
+  unsigned long long ctr[16];
+};
+
+}  // namespace fj

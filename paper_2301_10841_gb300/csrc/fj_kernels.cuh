@@ -1,0 +1,653 @@
+// Device kernels of libfj.
+//
+//  * COLT forcing (paper Section 4.2, Fig. 10 `force`): turn the child
+//    vectors of a list of parent entries into hash-map nodes of the next
+//    level, regrouping their offsets in place.  The root level is the same
+//    operation on the single virtual root entry, with the atom's pushed-down
+//    selections (Section 2.1) applied while scanning the base table.
+//  * Node expansion (Section 3.3 Fig. 7 with the batching of Section 4.3
+//    Fig. 11): iterate a batch of cover elements, probe every other subatom
+//    for the whole batch, drop misses, and hand the survivors to the next
+//    node, or aggregate / materialize them at the end of the plan.
+//  * Cover choice (Section 4.4): per partial tuple, the cover whose trie has
+//    the fewest keys; an unforced COLT vector is estimated by its length.
+//
+// Hashing uses the 64-bit finalizer of MurmurHash3 (Austin Appleby, public
+// domain) on a packed 64-bit key word (parent entry, key values).
+#pragma once
+
+#include <cstdint>
+
+#include "fj_internal.h"
+
+namespace fj {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// Key word of (parent, key tuple).  One level's keys all have the same arity:
+// 0 or 1 values are packed beside the parent; 2 values fill the word and are
+// only used where the parent is the single root entry.
+__device__ __forceinline__ uint64_t pack_key(uint32_t parent, int nk, int32_t v0, int32_t v1) {
+  if (nk == 2) return (uint64_t(uint32_t(v0)) << 32) | uint32_t(v1);
+  uint64_t w = uint64_t(parent) << 32;
+  if (nk == 1) w |= uint32_t(v0);
+  return w;
+}
+
+__device__ __forceinline__ uint32_t key_parent(uint64_t kw, int nk) {
+  return nk == 2 ? 0u : uint32_t(kw >> 32);
+}
+
+__device__ __forceinline__ int32_t key_value(uint64_t kw, int nk, int pos) {
+  if (nk == 2) return pos == 0 ? int32_t(uint32_t(kw >> 32)) : int32_t(uint32_t(kw));
+  return int32_t(uint32_t(kw));
+}
+
+__device__ __forceinline__ bool row_passes(const AtomDev& a, uint32_t row) {
+  for (int p = 0; p < a.n_preds; ++p) {
+    int32_t v = a.cols[a.pred_col[p]][row];
+    int32_t c = a.pred_val[p];
+    bool ok;
+    switch (a.pred_op[p]) {
+      case FJ_LT: ok = v < c; break;
+      case FJ_LE: ok = v <= c; break;
+      case FJ_GT: ok = v > c; break;
+      case FJ_GE: ok = v >= c; break;
+      case FJ_EQ: ok = v == c; break;
+      default: ok = v != c; break;
+    }
+    if (!ok) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  return (1u << lane_id()) - 1u;
+}
+
+// Hash-table slot access.  A slot is {key lo, key hi, entry, count}.
+__device__ __forceinline__ unsigned long long* slot_key(uint4* ht, uint32_t s) {
+  return reinterpret_cast<unsigned long long*>(&ht[s]);
+}
+
+// Insert kw; returns the slot and whether this thread claimed it.  Linear
+// probing bounded by the capacity (a full table sets kStTableFull).
+__device__ __forceinline__ uint32_t ht_insert(uint4* ht, uint32_t mask, uint64_t kw, bool& claimed,
+                                              uint32_t* status) {
+  claimed = false;
+  if (kw == kEmptyKey) {
+    uint32_t s = mask + 1;
+    claimed = atomicCAS(&ht[s].z, kNone, 0u) == kNone;
+    return s;
+  }
+  uint32_t h = uint32_t(mix64(kw)) & mask;
+  for (uint32_t it = 0; it <= mask; ++it) {
+    unsigned long long* kp = slot_key(ht, h);
+    unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(kp);
+    if (cur == kw) return h;
+    if (cur == kEmptyKey) {
+      unsigned long long old = atomicCAS(kp, kEmptyKey, kw);
+      if (old == kEmptyKey) {
+        claimed = true;
+        return h;
+      }
+      if (old == kw) return h;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicOr(status, kStTableFull);
+  return kNone;
+}
+
+// Read-only lookup: returns the slot contents' entry and count, or false.
+__device__ __forceinline__ bool ht_find(const uint4* __restrict__ ht, uint32_t mask, uint64_t kw,
+                                        uint32_t& e, uint32_t& cnt) {
+  if (kw == kEmptyKey) {
+    uint4 s = ht[mask + 1];
+    e = s.z;
+    cnt = s.w;
+    return s.w != 0;
+  }
+  uint32_t h = uint32_t(mix64(kw)) & mask;
+  for (uint32_t it = 0; it <= mask; ++it) {
+    uint4 s = __ldg(&ht[h]);
+    uint64_t k = (uint64_t(s.y) << 32) | s.x;
+    if (k == kw) {
+      e = s.z;
+      cnt = s.w;
+      return true;
+    }
+    if (k == kEmptyKey) return false;
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+// Wide slots: slot s occupies ht[2s] (key: parent, k0, k1, k2) and ht[2s+1]
+// (entry, count).  The parent word is below 2^32 - 1, so no real key equals
+// the all-ones empty marker.
+struct alignas(16) Key128 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ bool key128_eq(const uint4& a, const uint4& b) {
+  return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
+}
+
+__device__ __forceinline__ uint64_t mix128(const uint4& k) {
+  return mix64((uint64_t(k.x) << 32 | k.y) ^ mix64(uint64_t(k.z) << 32 | k.w));
+}
+
+// Insert into a wide level.  Every probe of a slot is a 16-byte CAS, so a
+// half-written key is never observed.
+__device__ __forceinline__ uint32_t ht_insert_wide(uint4* ht, uint32_t mask, uint4 kw, bool& claimed,
+                                                   uint32_t* status) {
+  claimed = false;
+  uint32_t h = uint32_t(mix128(kw)) & mask;
+  const Key128 empty{kNone, kNone, kNone, kNone};
+  const Key128 want{kw.x, kw.y, kw.z, kw.w};
+  for (uint32_t it = 0; it <= mask; ++it) {
+    Key128* kp = reinterpret_cast<Key128*>(&ht[2 * size_t(h)]);
+    Key128 old = atomicCAS(kp, empty, want);
+    if (old.x == kNone && old.y == kNone && old.z == kNone && old.w == kNone) {
+      claimed = true;
+      return h;
+    }
+    if (old.x == kw.x && old.y == kw.y && old.z == kw.z && old.w == kw.w) return h;
+    h = (h + 1) & mask;
+  }
+  atomicOr(status, kStTableFull);
+  return kNone;
+}
+
+__device__ __forceinline__ bool ht_find_wide(const uint4* __restrict__ ht, uint32_t mask, uint4 kw,
+                                             uint32_t& e, uint32_t& cnt) {
+  uint32_t h = uint32_t(mix128(kw)) & mask;
+  for (uint32_t it = 0; it <= mask; ++it) {
+    uint4 k = __ldg(&ht[2 * size_t(h)]);
+    if (key128_eq(k, kw)) {
+      uint4 v = __ldg(&ht[2 * size_t(h) + 1]);
+      e = v.x;
+      cnt = v.y;
+      return true;
+    }
+    if (k.x == kNone && k.y == kNone && k.z == kNone && k.w == kNone) return false;
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+// Entry / count fields of slot s of a level.
+__device__ __forceinline__ uint32_t* slot_e(uint4* ht, int wide, uint32_t s) {
+  return wide ? &ht[2 * size_t(s) + 1].x : &ht[s].z;
+}
+__device__ __forceinline__ uint32_t* slot_cnt(uint4* ht, int wide, uint32_t s) {
+  return wide ? &ht[2 * size_t(s) + 1].y : &ht[s].w;
+}
+
+// ---------------------------------------------------------------------------
+// Block-level helpers.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane_id() >= uint32_t(o)) v += n;
+  }
+  return v;
+}
+
+// Exclusive block scan of one value per thread; returns the prefix and
+// writes the block total to *total.  Uses `sh` (>= 33 elements).
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* sh, T* total) {
+  T inc = warp_incl_scan(v);
+  int w = threadIdx.x >> 5;
+  if (lane_id() == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    T x = lane_id() < uint32_t(nw) ? sh[lane_id()] : T(0);
+    T xi = warp_incl_scan(x);
+    if (lane_id() < uint32_t(nw)) sh[lane_id()] = xi - x;
+    if (lane_id() == uint32_t(nw - 1)) sh[32] = xi;
+  }
+  __syncthreads();
+  T out = sh[w] + inc - v;
+  *total = sh[32];
+  __syncthreads();
+  return out;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  T tot;
+  block_excl_scan(v, sh, &tot);
+  return tot;
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scans (three passes, device-side lengths, one scan
+// per blockIdx.y job).  The Op supplies n(job), load(job, i) and
+// store(job, i, prefix) and receives the total.
+// ---------------------------------------------------------------------------
+
+constexpr int kScanBlocks = 608;  // 4 per SM
+
+template <typename T, typename Op>
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(Op op, T* partials) {
+  int job = blockIdx.y;
+  uint64_t n = op.n(job);
+  uint64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  uint64_t lo = chunk * blockIdx.x, hi = min(n, lo + chunk);
+  T acc = 0;
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += op.load(job, i);
+  __shared__ T sh[33];
+  T tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[size_t(job) * kScanBlocks + blockIdx.x] = tot;
+}
+
+template <typename T, typename Op>
+__global__ void __launch_bounds__(1024) k_scan_mid(Op op, T* partials, int nb) {
+  int job = blockIdx.y;
+  __shared__ T sh[33];
+  T* p = partials + size_t(job) * kScanBlocks;
+  T carry = 0;
+  for (int base = 0; base < nb; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    T v = i < nb ? p[i] : T(0);
+    T tot;
+    T ex = block_excl_scan(v, sh, &tot);
+    if (i < nb) p[i] = ex + carry;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) op.total(job, carry);
+}
+
+template <typename T, typename Op>
+__global__ void __launch_bounds__(kThreads) k_scan_down(Op op, const T* partials) {
+  int job = blockIdx.y;
+  uint64_t n = op.n(job);
+  uint64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  uint64_t lo = chunk * blockIdx.x, hi = min(n, lo + chunk);
+  __shared__ T sh[33];
+  T carry = partials[size_t(job) * kScanBlocks + blockIdx.x];
+  for (uint64_t base = lo; base < hi; base += blockDim.x) {
+    uint64_t i = base + threadIdx.x;
+    T v = i < hi ? op.load(job, i) : T(0);
+    T tot;
+    T ex = block_excl_scan(v, sh, &tot);
+    if (i < hi) op.store(job, i, ex + carry);
+    carry += tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// COLT forcing.  A job is (atom, level i >= 1): build the map nodes of L[i]
+// for the parents of L[i-1] listed in L[i].req.
+// ---------------------------------------------------------------------------
+
+struct ForceJobs {
+  AtomDev* atoms;
+  const int2* jobs;  // (atom, level)
+  int n_jobs;
+};
+
+// Rows a job regroups: the root (level 1, relation not yet materialized)
+// scans the whole base table; otherwise the parents' ranges of perm.
+__device__ __forceinline__ bool job_identity(const AtomDev& a, int lvl) {
+  return lvl == 1 && !a.root_mat;
+}
+
+// Pass 0a: rows that will be inserted (identity root jobs count the rows
+// passing the selection; deeper levels use the root's passing-row count).
+__global__ void __launch_bounds__(kThreads) k_force_count(ForceJobs fj) {
+  int2 jb = fj.jobs[blockIdx.y];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  if (L.n_req == 0 || L.cleared) return;
+  if (!job_identity(a, jb.y)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) L.n_in = a.n_pass;
+    return;
+  }
+  if (a.n_preds == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) L.n_in = a.n_rows;
+    return;
+  }
+  __shared__ uint32_t sh[33];
+  uint32_t c = 0;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n_rows; r += gridDim.x * blockDim.x)
+    c += row_passes(a, r);
+  uint32_t tot = block_sum(c, sh);
+  if (threadIdx.x == 0 && tot) atomicAdd(&L.n_in, tot);
+}
+
+// Pass 0b: size the table of a level the first time it is forced.
+__global__ void k_force_prepare(ForceJobs fj) {
+  int2 jb = fj.jobs[blockIdx.x];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  if (L.n_req == 0 || L.cleared || threadIdx.x != 0) return;
+  float want = float(L.n_in) / (a.load > 0.f ? a.load : 0.5f);
+  uint32_t cap = 16;
+  while (float(cap) < want && cap < L.ht_cap_max) cap <<= 1;
+  L.mask = cap - 1;
+}
+
+// Pass 1: clear a level's table the first time it is forced.
+__global__ void k_force_clear(ForceJobs fj) {
+  int2 jb = fj.jobs[blockIdx.y];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  if (L.n_req == 0 || L.cleared) return;
+  uint32_t n = L.mask + 2;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (L.wide) {
+      L.ht[2 * size_t(i)] = make_uint4(kNone, kNone, kNone, kNone);
+      L.ht[2 * size_t(i) + 1] = make_uint4(kNone, 0u, 0u, 0u);
+    } else {
+      L.ht[i] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
+    }
+  }
+}
+
+// Scan op: row offsets of the requested parents.
+struct RowOffOp {
+  AtomDev* atoms;
+  const int2* jobs;
+  __device__ uint64_t n(int job) const {
+    int2 jb = jobs[job];
+    return atoms[jb.x].L[jb.y].n_req;
+  }
+  __device__ uint32_t load(int job, uint64_t i) const {
+    int2 jb = jobs[job];
+    const AtomDev& a = atoms[jb.x];
+    const LevelDev& L = a.L[jb.y];
+    if (job_identity(a, jb.y)) return a.n_rows;
+    return a.L[jb.y - 1].count[L.req[i]];
+  }
+  __device__ void store(int job, uint64_t i, uint32_t v) const {
+    int2 jb = jobs[job];
+    atoms[jb.x].L[jb.y].rowoff[i] = v;
+  }
+  __device__ void total(int job, uint32_t v) const {
+    int2 jb = jobs[job];
+    LevelDev& L = atoms[jb.x].L[jb.y];
+    L.n_rows = v;
+    L.rowoff[L.n_req] = v;
+    L.n_new = 0;
+    L.base = L.n_entries;
+  }
+};
+
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t n, uint32_t x) {
+  // first index i in [0, n) with a[i] > x
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Pass 2: insert every row's (parent, key) and count it.
+__global__ void __launch_bounds__(kThreads) k_force_insert(ForceJobs fj, ResultDev* res) {
+  int2 jb = fj.jobs[blockIdx.y];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  LevelDev& P = a.L[jb.y - 1];
+  uint32_t nreq = L.n_req;
+  if (nreq == 0) return;
+  uint32_t n = L.n_rows;
+  bool ident = job_identity(a, jb.y);
+  uint32_t mask = L.mask;
+  int nk = L.nk;
+  int wide = L.wide;
+  const int32_t* c0 = a.cols[L.kcol[0]];
+  const int32_t* c1 = a.cols[L.kcol[1]];
+  const int32_t* c2 = a.cols[L.kcol[2]];
+  uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t start = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+  for (uint32_t base = start; base < n; base += stride) {
+    uint32_t t = base + lane_id();
+    bool active = t < n;
+    uint32_t row = 0, parent = 0, slot = kNone;
+    bool claimed = false;
+    if (active) {
+      if (ident) {
+        row = t;
+        active = row_passes(a, row);
+      } else {
+        uint32_t pi = upper_bound_u32(L.rowoff, nreq, t) - 1;
+        parent = L.req[pi];
+        row = a.perm[P.begin[parent] + (t - L.rowoff[pi])];
+      }
+    }
+    if (active) {
+      if (wide) {
+        uint4 kw = make_uint4(parent, nk > 0 ? uint32_t(c0[row]) : 0u,
+                              nk > 1 ? uint32_t(c1[row]) : 0u, nk > 2 ? uint32_t(c2[row]) : 0u);
+        slot = ht_insert_wide(L.ht, mask, kw, claimed, &res->status);
+      } else {
+        uint64_t kw = pack_key(parent, nk, nk > 0 ? c0[row] : 0, nk > 1 ? c1[row] : 0);
+        slot = ht_insert(L.ht, mask, kw, claimed, &res->status);
+      }
+      if (slot == kNone) active = false;
+    }
+    // Claimed slots: one local index per parent (grouped per warp), and an
+    // append to the new-slot list.
+    uint32_t cmask = __ballot_sync(0xffffffffu, claimed);
+    if (claimed) {
+      uint32_t grp = __match_any_sync(cmask, parent);
+      uint32_t leader = __ffs(grp) - 1;
+      uint32_t rank = __popc(grp & lanemask_lt());
+      uint32_t first = 0;
+      if (lane_id() == leader) first = atomicAdd(&P.child_nkeys[parent], __popc(grp));
+      first = __shfl_sync(grp, first, leader);
+      *slot_e(L.ht, wide, slot) = first + rank;
+      uint32_t wl = __ffs(cmask) - 1;
+      uint32_t pos = 0;
+      if (lane_id() == wl) pos = atomicAdd(&L.n_new, __popc(cmask));
+      pos = __shfl_sync(cmask, pos, wl);
+      a.newslots[pos + __popc(cmask & lanemask_lt())] = slot;
+    }
+    uint32_t amask = __ballot_sync(0xffffffffu, active);
+    if (active) {
+      uint32_t grp = __match_any_sync(amask, slot);
+      if (lane_id() == __ffs(grp) - 1) atomicAdd(slot_cnt(L.ht, wide, slot), __popc(grp));
+    }
+    if (t < n) {
+      a.tmp_row[t] = row;
+      a.tmp_slot[t] = active ? slot : kNone;
+    }
+  }
+}
+
+// Scan op: first child entry of each requested parent.
+struct ChildFirstOp {
+  AtomDev* atoms;
+  const int2* jobs;
+  __device__ uint64_t n(int job) const {
+    int2 jb = jobs[job];
+    return atoms[jb.x].L[jb.y].n_req;
+  }
+  __device__ uint32_t load(int job, uint64_t i) const {
+    int2 jb = jobs[job];
+    const AtomDev& a = atoms[jb.x];
+    return a.L[jb.y - 1].child_nkeys[a.L[jb.y].req[i]];
+  }
+  __device__ void store(int job, uint64_t i, uint32_t v) const {
+    int2 jb = jobs[job];
+    AtomDev& a = atoms[jb.x];
+    a.L[jb.y - 1].child_first[a.L[jb.y].req[i]] = a.L[jb.y].base + v;
+  }
+  __device__ void total(int job, uint32_t) const {}
+};
+
+// Pass 3: give each new slot its entry id and fill the entry arrays.
+__global__ void __launch_bounds__(kThreads) k_force_assign(ForceJobs fj) {
+  int2 jb = fj.jobs[blockIdx.y];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  const LevelDev& P = a.L[jb.y - 1];
+  if (L.n_req == 0) return;
+  uint32_t nnew = L.n_new;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nnew; i += gridDim.x * blockDim.x) {
+    uint32_t s = a.newslots[i];
+    uint64_t kw;
+    uint32_t parent, local, cnt;
+    if (L.wide) {
+      uint4 k = L.ht[2 * size_t(s)];
+      uint4 v = L.ht[2 * size_t(s) + 1];
+      parent = k.x;
+      kw = uint64_t(parent) << 32;  // wide entries keep only the parent
+      local = v.x;
+      cnt = v.y;
+    } else {
+      uint4 sl = L.ht[s];
+      kw = s == L.mask + 1 ? kEmptyKey : ((uint64_t(sl.y) << 32) | sl.x);
+      parent = key_parent(kw, L.nk);
+      local = sl.z;
+      cnt = sl.w;
+    }
+    uint32_t e = P.child_first[parent] + local;
+    *slot_e(L.ht, L.wide, s) = e;
+    L.key[e] = kw;
+    L.count[e] = cnt;
+    L.fill[e] = 0;
+    if (L.child_state) L.child_state[e] = kUnforced;
+    if (L.child_nkeys) L.child_nkeys[e] = 0;
+  }
+}
+
+// Scan op: relative start of each new entry's vector, written into begin[]
+// (k_force_begin turns it into an absolute cursor in fill[]).
+struct EntryPosOp {
+  AtomDev* atoms;
+  const int2* jobs;
+  __device__ uint64_t n(int job) const {
+    int2 jb = jobs[job];
+    const LevelDev& L = atoms[jb.x].L[jb.y];
+    return L.n_req ? L.n_new : 0;
+  }
+  __device__ uint32_t load(int job, uint64_t i) const {
+    int2 jb = jobs[job];
+    const LevelDev& L = atoms[jb.x].L[jb.y];
+    return L.count[L.base + i];
+  }
+  __device__ void store(int job, uint64_t i, uint32_t v) const {
+    int2 jb = jobs[job];
+    const LevelDev& L = atoms[jb.x].L[jb.y];
+    L.begin[L.base + i] = v;
+  }
+  __device__ void total(int job, uint32_t v) const {
+    int2 jb = jobs[job];
+    atoms[jb.x].L[jb.y].pos_total = v;
+  }
+};
+
+// Pass 4: absolute write cursor of each new entry, inside its parent's range:
+// fill[e] = parent begin + (relative start of e - relative start of the
+// parent's first child).  Reads begin[], writes fill[] only.
+__global__ void __launch_bounds__(kThreads) k_force_begin(ForceJobs fj) {
+  int2 jb = fj.jobs[blockIdx.y];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  const LevelDev& P = a.L[jb.y - 1];
+  if (L.n_req == 0) return;
+  uint32_t nnew = L.n_new;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nnew; i += gridDim.x * blockDim.x) {
+    uint32_t e = L.base + i;
+    uint32_t parent = L.wide ? uint32_t(L.key[e] >> 32) : key_parent(L.key[e], L.nk);
+    uint32_t first = P.child_first[parent];
+    uint32_t pstart = (jb.y == 1 && !a.root_mat) ? 0u : P.begin[parent];
+    L.fill[e] = pstart + (L.begin[e] - L.begin[first]);
+  }
+}
+
+// Pass 5: move every row to its entry's range (fill[] is the cursor).
+__global__ void __launch_bounds__(kThreads) k_force_scatter(ForceJobs fj) {
+  int2 jb = fj.jobs[blockIdx.y];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  if (L.n_req == 0) return;
+  uint32_t n = L.n_rows;
+  uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t start = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+  for (uint32_t base = start; base < n; base += stride) {
+    uint32_t t = base + lane_id();
+    uint32_t slot = t < n ? a.tmp_slot[t] : kNone;
+    bool active = slot != kNone;
+    uint32_t e = active ? *slot_e(L.ht, L.wide, slot) : 0;
+    uint32_t amask = __ballot_sync(0xffffffffu, active);
+    if (active) {
+      uint32_t grp = __match_any_sync(amask, e);
+      uint32_t leader = __ffs(grp) - 1;
+      uint32_t first = 0;
+      if (lane_id() == leader) first = atomicAdd(&L.fill[e], __popc(grp));
+      first = __shfl_sync(grp, first, leader);
+      a.perm[first + __popc(grp & lanemask_lt())] = a.tmp_row[t];
+    }
+  }
+}
+
+// Pass 6: bookkeeping.  begin[e] = cursor - count; requested parents are
+// forced; the root range is now materialized (perm[0..n_pass) holds exactly
+// the rows that pass the selection).
+__global__ void __launch_bounds__(kThreads) k_force_finish(ForceJobs fj, ResultDev* res) {
+  int2 jb = fj.jobs[blockIdx.y];
+  AtomDev& a = fj.atoms[jb.x];
+  LevelDev& L = a.L[jb.y];
+  LevelDev& P = a.L[jb.y - 1];
+  uint32_t nreq = L.n_req;
+  if (nreq == 0) return;
+  uint32_t nnew = L.n_new;
+  uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (uint32_t i = tid; i < nnew; i += stride) {
+    uint32_t e = L.base + i;
+    L.begin[e] = L.fill[e] - L.count[e];
+  }
+  for (uint32_t i = tid; i < nreq; i += stride) P.child_state[L.req[i]] = kForced;
+  if (tid == 0) {
+    if (jb.y == 1) {
+      a.n_pass = L.pos_total;
+      a.root_mat = 1;
+      P.begin[0] = 0;
+      P.count[0] = L.pos_total;
+      atomicAdd(&res->ctr[FJ_CTR_ROOTS_BUILT], 1ull);
+      atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
+               1ull << jb.x);
+    } else {
+      atomicAdd(&res->ctr[FJ_CTR_SUBTRIES_FORCED], (unsigned long long)nreq);
+    }
+    atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)L.pos_total);
+    L.n_entries = L.base + nnew;
+    L.cleared = 1;
+  }
+}
+
+// The next force of this level starts with an empty request list.  Runs after
+// k_force_finish (a separate launch so no block still reads n_req).
+__global__ void k_force_reset_req(ForceJobs fj) {
+  int2 jb = fj.jobs[blockIdx.x];
+  if (threadIdx.x == 0) {
+    fj.atoms[jb.x].L[jb.y].n_req = 0;
+    fj.atoms[jb.x].L[jb.y].n_in = 0;
+  }
+}
+
+}  // namespace fj

@@ -1,0 +1,47 @@
+// Host-side Free Join plan logic (paper Section 3.2 and Section 4.1).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/fj.h"
+
+namespace fj {
+
+// A subatom with its variables in the atom's column order.
+struct PSub {
+  int atom;
+  std::vector<int> vars;
+};
+using PNode = std::vector<PSub>;
+using PPlan = std::vector<PNode>;
+
+struct PQuery {
+  std::vector<std::vector<int>> atom_vars;  // per atom, in column order
+  std::vector<int> head;                    // output variable order
+};
+
+// Thread-local error message shared by every entry point.
+void set_error(const std::string& msg);
+const char* get_error();
+
+bool load_query(const fj_query* q, PQuery& out);
+bool load_plan(const PQuery& q, const fj_plan* p, PPlan& out);
+
+uint64_t vs_mask(const PNode& node);
+uint64_t avs_mask(const PPlan& plan, int k);
+std::vector<int> covers(const PPlan& plan, int k);
+
+// Def. 3.3 / Def. 3.4, plus: sub[0] of every node is a cover.
+bool validate(const PQuery& q, const PPlan& plan);
+
+PPlan binary2fj(const PQuery& q, const std::vector<int>& order);
+PPlan factor(const PPlan& plan);
+
+// GHT schema of one atom (Section 3.3): levels and whether the trailing
+// empty level is present.
+std::vector<std::vector<int>> ght_schema(const PPlan& plan, int atom);
+
+fj_plan* export_plan(const PPlan& plan);
+
+}  // namespace fj

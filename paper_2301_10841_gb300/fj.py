@@ -1,0 +1,395 @@
+"""ctypes binding of libfj.so (declared in include/fj.h).
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels.  Importing this module loads ``libfj.so`` and raises ImportError if it
+is missing -- there is no fallback.
+
+Queries use plain data: an atom is a dict with ``rel`` (a :class:`Relation`),
+``vars`` (distinct variable ids), optional ``rel_cols`` (column of the relation
+per variable) and optional ``preds`` (``(j, op, value)`` with ``op`` one of
+``"<" "<=" ">" ">=" "==" "!="``).  A plan is a list of nodes, a node a list of
+``(atom_index, vars)`` subatoms whose first entry is the node's cover.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libfj.so")
+if not os.path.exists(_SO):
+    raise ImportError(f"libfj.so not built ({_SO}); run __graft_entry__.build()")
+_lib = ctypes.CDLL(_SO)
+
+MAX_VARS = 32
+OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
+COVER = {"static": 0, "fewest": 1, "learned": 2}
+OUT = {"materialize": 0, "count": 1, "count_min": 2}
+FLAG_EAGER_ALL = 1
+FLAG_EAGER_ROOT = 2
+CTR = {"cover_iters": 0, "probes": 1, "probe_hits": 2, "roots_built": 3, "subtries_forced": 4,
+       "rows_regrouped": 5, "survivors": 6, "chunks": 7, "kernels": 8, "atom_built_mask": 9}
+
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "INVALID_PLAN", -3: "OOM", -4: "OUTPUT_OVERFLOW",
+          -5: "COUNT_OVERFLOW", -6: "TIMEOUT", -7: "CUDA", -8: "UNSUPPORTED"}
+
+
+class FJError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{ERRORS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Pred(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int), ("op", ctypes.c_int), ("value", ctypes.c_int32)]
+
+
+class _Atom(ctypes.Structure):
+    _fields_ = [("rel", ctypes.c_void_p), ("n_vars", ctypes.c_int),
+                ("vars", ctypes.POINTER(ctypes.c_int)), ("cols", ctypes.POINTER(ctypes.c_int)),
+                ("n_preds", ctypes.c_int), ("preds", ctypes.POINTER(_Pred))]
+
+
+class _Query(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("atoms", ctypes.POINTER(_Atom)),
+                ("n_head", ctypes.c_int), ("head_vars", ctypes.POINTER(ctypes.c_int))]
+
+
+class _Sub(ctypes.Structure):
+    _fields_ = [("atom", ctypes.c_int), ("n_vars", ctypes.c_int),
+                ("vars", ctypes.POINTER(ctypes.c_int))]
+
+
+class _Node(ctypes.Structure):
+    _fields_ = [("n_sub", ctypes.c_int), ("sub", ctypes.POINTER(_Sub))]
+
+
+class _Plan(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int), ("nodes", ctypes.POINTER(_Node))]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("batch_size", ctypes.c_uint32), ("load_factor", ctypes.c_float),
+                ("cover_policy", ctypes.c_int), ("out_mode", ctypes.c_int),
+                ("list_limit", ctypes.c_uint64), ("n_min_vars", ctypes.c_int),
+                ("min_vars", ctypes.POINTER(ctypes.c_int)), ("spin_limit", ctypes.c_uint64),
+                ("model", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("mins", ctypes.c_int32 * MAX_VARS),
+                ("min_valid", ctypes.c_uint8 * MAX_VARS), ("n_head", ctypes.c_int),
+                ("n_out", ctypes.c_uint64), ("d_tuples", ctypes.c_void_p),
+                ("tuples_owned", ctypes.c_int), ("counters", ctypes.c_uint64 * 16)]
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_sig = {
+    "fj_ctx_create": ([ctypes.c_int, _vp, _P(_vp)], ctypes.c_int),
+    "fj_ctx_destroy": ([_vp], None),
+    "fj_ctx_set_stream": ([_vp, _vp], ctypes.c_int),
+    "fj_last_error": ([], ctypes.c_char_p),
+    "fj_load_relation": ([_vp, ctypes.c_char_p, ctypes.c_int, _P(_vp), ctypes.c_uint64, _P(_vp)],
+                         ctypes.c_int),
+    "fj_load_relation_host": ([_vp, ctypes.c_char_p, ctypes.c_int, _P(_vp), ctypes.c_uint64,
+                               _P(_vp)], ctypes.c_int),
+    "fj_release_relation": ([_vp, _vp], None),
+    "fj_relation_rows": ([_vp], ctypes.c_uint64),
+    "fj_validate_plan": ([_P(_Query), _P(_Plan)], ctypes.c_int),
+    "fj_binary_to_free_plan": ([_P(_Query), _P(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                _P(_P(_Plan))], ctypes.c_int),
+    "fj_plan_free": ([_P(_Plan)], None),
+    "fj_ght_schema": ([_P(_Query), _P(_Plan), ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int),
+                       _P(ctypes.c_int)], ctypes.c_int),
+    "fj_node_covers": ([_P(_Query), _P(_Plan), ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)],
+                       ctypes.c_int),
+    "fj_execute_plan": ([_vp, _P(_Query), _P(_Plan), _P(_Opts), _P(_Result)], ctypes.c_int),
+    "fj_prepare": ([_vp, _P(_Query), _P(_Plan), _P(_Opts), _P(_vp)], ctypes.c_int),
+    "fj_build_colt_level": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "fj_execute_prepared": ([_vp, _P(_Result)], ctypes.c_int),
+    "fj_reset_prepared": ([_vp], ctypes.c_int),
+    "fj_prepared_free": ([_vp], None),
+    "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
+    "fj_result_free": ([_vp, _P(_Result)], None),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = sorted(_sig)
+
+
+def _check(st):
+    if st != 0:
+        raise FJError(st, _lib.fj_last_error().decode())
+
+
+def _ints(xs):
+    xs = [int(x) for x in xs]
+    return (ctypes.c_int * max(1, len(xs)))(*xs)
+
+
+# ---------------------------------------------------------------------------
+# Marshalling of queries and plans.
+# ---------------------------------------------------------------------------
+
+class _QueryC:
+    """Keeps the ctypes arrays of one query alive."""
+
+    def __init__(self, atoms, head=None):
+        self.keep = []
+        arr = (_Atom * len(atoms))()
+        for i, a in enumerate(atoms):
+            vs = _ints(a["vars"])
+            cols = a.get("rel_cols")
+            cp = _ints(cols) if cols is not None else None
+            preds = a.get("preds", [])
+            pa = (_Pred * max(1, len(preds)))(*[_Pred(int(j), OPS[op], int(v)) for j, op, v in preds])
+            rel = a.get("rel")
+            handle = rel.handle if isinstance(rel, Relation) else None
+            arr[i] = _Atom(handle, len(a["vars"]), ctypes.cast(vs, _P(ctypes.c_int)),
+                           ctypes.cast(cp, _P(ctypes.c_int)) if cp is not None else None,
+                           len(preds), ctypes.cast(pa, _P(_Pred)))
+            self.keep += [vs, cp, pa]
+        self.arr = arr
+        self.head = None if head is None else _ints(head)
+        self.q = _Query(len(atoms), ctypes.cast(arr, _P(_Atom)), 0 if head is None else len(head),
+                        None if head is None else ctypes.cast(self.head, _P(ctypes.c_int)))
+
+    @property
+    def ptr(self):
+        return ctypes.byref(self.q)
+
+
+class _PlanC:
+    def __init__(self, plan):
+        self.keep = []
+        nodes = (_Node * len(plan))()
+        for k, node in enumerate(plan):
+            subs = (_Sub * len(node))()
+            for s, (atom, vars_) in enumerate(node):
+                vs = _ints(vars_)
+                self.keep.append(vs)
+                subs[s] = _Sub(int(atom), len(vars_), ctypes.cast(vs, _P(ctypes.c_int)))
+            self.keep.append(subs)
+            nodes[k] = _Node(len(node), ctypes.cast(subs, _P(_Sub)))
+        self.nodes = nodes
+        self.p = _Plan(len(plan), ctypes.cast(nodes, _P(_Node)))
+
+    @property
+    def ptr(self):
+        return ctypes.byref(self.p)
+
+
+def _plan_from_c(pp):
+    p = pp.contents
+    out = []
+    for k in range(p.n_nodes):
+        n = p.nodes[k]
+        out.append([(n.sub[s].atom, tuple(n.sub[s].vars[j] for j in range(n.sub[s].n_vars)))
+                    for s in range(n.n_sub)])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Plans (host only; no GPU needed).
+# ---------------------------------------------------------------------------
+
+def binary_to_free_plan(atoms, order=None, factor=True):
+    """binary2fj (Fig. 12) and, if ``factor``, factor (Fig. 13)."""
+    q = _QueryC(atoms)
+    order = list(range(len(atoms))) if order is None else list(order)
+    out = _P(_Plan)()
+    _check(_lib.fj_binary_to_free_plan(q.ptr, _ints(order), len(order), int(bool(factor)),
+                                       ctypes.byref(out)))
+    try:
+        return _plan_from_c(out)
+    finally:
+        _lib.fj_plan_free(out)
+
+
+def validate_plan(atoms, plan):
+    """Returns (True, "") or (False, reason) per Def. 3.3 / Def. 3.4."""
+    q, p = _QueryC(atoms), _PlanC(plan)
+    st = _lib.fj_validate_plan(q.ptr, p.ptr)
+    return st == 0, _lib.fj_last_error().decode()
+
+
+def ght_schema(atoms, plan, atom):
+    q, p = _QueryC(atoms), _PlanC(plan)
+    n = ctypes.c_int(0)
+    sizes = (ctypes.c_int * 64)()
+    vs = (ctypes.c_int * 64)()
+    _check(_lib.fj_ght_schema(q.ptr, p.ptr, atom, ctypes.byref(n), sizes, vs))
+    out, w = [], 0
+    for lv in range(n.value):
+        out.append([vs[w + j] for j in range(sizes[lv])])
+        w += sizes[lv]
+    return out
+
+
+def node_covers(atoms, plan, k):
+    q, p = _QueryC(atoms), _PlanC(plan)
+    n = ctypes.c_int(0)
+    cv = (ctypes.c_int * 64)()
+    _check(_lib.fj_node_covers(q.ptr, p.ptr, k, ctypes.byref(n), cv))
+    return [cv[i] for i in range(n.value)]
+
+
+# ---------------------------------------------------------------------------
+# Context, relations, execution.
+# ---------------------------------------------------------------------------
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """A libfj context on one CUDA device, enqueuing on a torch stream."""
+
+    def __init__(self, device=0, stream=None):
+        self.handle = _vp()
+        if stream is None:
+            stream = _current_stream()
+        _check(_lib.fj_ctx_create(int(device), _vp(stream), ctypes.byref(self.handle)))
+        self.device = device
+
+    def set_stream(self, stream):
+        _check(_lib.fj_ctx_set_stream(self.handle, _vp(stream)))
+
+    def relation(self, cols, name=""):
+        """Borrow device columns (torch int32 CUDA tensors of equal length)."""
+        return Relation(self, cols, name, host=False)
+
+    def relation_host(self, cols, name=""):
+        """Copy host columns (numpy int32 arrays or CPU tensors) to the device."""
+        return Relation(self, cols, name, host=True)
+
+    def close(self):
+        if self.handle:
+            _lib.fj_ctx_destroy(self.handle)
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Relation:
+    def __init__(self, ctx, cols, name="", host=False):
+        self.ctx = ctx
+        self.keep = list(cols)
+        ptrs = []
+        n = None
+        for c in cols:
+            if hasattr(c, "data_ptr"):
+                if c.dtype.__str__() != "torch.int32" or not c.is_contiguous():
+                    raise ValueError("columns must be contiguous int32")
+                ptrs.append(c.data_ptr())
+                length = c.numel()
+            else:
+                c = np.ascontiguousarray(c, dtype=np.int32)
+                self.keep.append(c)
+                ptrs.append(c.ctypes.data)
+                length = len(c)
+            if n is None:
+                n = length
+            elif n != length:
+                raise ValueError("columns of one relation must have equal length")
+        arr = (_vp * len(ptrs))(*ptrs)
+        self.handle = _vp()
+        fn = _lib.fj_load_relation_host if host else _lib.fj_load_relation
+        _check(fn(ctx.handle, name.encode(), len(ptrs), arr, int(n or 0), ctypes.byref(self.handle)))
+        self.n_rows = int(n or 0)
+
+    def release(self):
+        if self.handle:
+            _lib.fj_release_relation(self.ctx.handle, self.handle)
+            self.handle = _vp()
+
+
+class Result:
+    def __init__(self, res, tuples, min_vars):
+        self.count = int(res.count)
+        self.mins = [int(res.mins[i]) if res.min_valid[i] else None for i in range(len(min_vars))]
+        self.tuples = tuples
+        self.counters = {k: int(res.counters[v]) for k, v in CTR.items()}
+
+
+def _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags):
+    mv = _ints(min_vars or [])
+    o = _Opts(int(batch_size), float(load_factor), COVER[cover], OUT[out_mode], int(list_limit),
+              len(min_vars or []), ctypes.cast(mv, _P(ctypes.c_int)), 0, None, int(flags))
+    return o, mv
+
+
+def _take_tuples(ctx, res, n_head):
+    import torch
+    n = int(res.n_out)
+    t = torch.empty((n, n_head), dtype=torch.int32, device=f"cuda:{ctx.device}")
+    if n:
+        _check(_lib.fj_result_copy_tuples(ctx.handle, ctypes.byref(res), _vp(t.data_ptr()), 1))
+    return t
+
+
+def execute(ctx, atoms, plan, head=None, out_mode="count", min_vars=None, batch_size=0,
+            load_factor=0.0, cover="static", list_limit=0, flags=0):
+    """One-shot fj_execute_plan.  Returns a :class:`Result`; materialized
+    tuples come back as an (n, len(head)) int32 CUDA tensor in head order
+    (unsorted)."""
+    q, p = _QueryC(atoms, head), _PlanC(plan)
+    o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags)
+    res = _Result()
+    _check(_lib.fj_execute_plan(ctx.handle, q.ptr, p.ptr, ctypes.byref(o), ctypes.byref(res)))
+    tuples = None
+    try:
+        if out_mode == "materialize":
+            tuples = _take_tuples(ctx, res, res.n_head)
+    finally:
+        _lib.fj_result_free(ctx.handle, ctypes.byref(res))
+    return Result(res, tuples, min_vars or [])
+
+
+class Prepared:
+    """fj_prepare / fj_build_colt_level / fj_execute_prepared / fj_reset_prepared."""
+
+    def __init__(self, ctx, atoms, plan, head=None, out_mode="count", min_vars=None,
+                 batch_size=0, load_factor=0.0, cover="static", list_limit=0, flags=0):
+        self.ctx = ctx
+        self.min_vars = list(min_vars or [])
+        self.out_mode = out_mode
+        q, p = _QueryC(atoms, head), _PlanC(plan)
+        o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags)
+        self.handle = _vp()
+        _check(_lib.fj_prepare(ctx.handle, q.ptr, p.ptr, ctypes.byref(o), ctypes.byref(self.handle)))
+
+    def build_level(self, atom, level):
+        _check(_lib.fj_build_colt_level(self.handle, int(atom), int(level)))
+
+    def execute(self):
+        res = _Result()
+        _check(_lib.fj_execute_prepared(self.handle, ctypes.byref(res)))
+        tuples = _take_tuples(self.ctx, res, res.n_head) if self.out_mode == "materialize" else None
+        return Result(res, tuples, self.min_vars)
+
+    def reset(self):
+        _check(_lib.fj_reset_prepared(self.handle))
+
+    def free(self):
+        if self.handle:
+            _lib.fj_prepared_free(self.handle)
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
