@@ -1,0 +1,399 @@
+"""Free Join on GB300: throughput of the star-join workload.
+
+Workload (one step = the whole hot path, from the base tables): fact table F
+with 10,000,000 rows of 4 int32 foreign keys, each Zipf(s=1.1) over its
+dimension's keys; dimensions D1..D4 of 100K / 250K / 500K / 1M rows (int32
+key, int32 attribute) with the selection attribute < 1e8 (10%).  The
+left-deep plan [F, D1, D2, D3, D4] is converted by binary2fj and factored;
+every step builds the COLT levels it needs from scratch and returns COUNT(*)
+and MIN of each dimension attribute.
+
+Metric: input + output tuples per second (inputs = rows of every atom,
+outputs = COUNT), with the inputs resident in HBM; `e2e` repeats it through
+the public API from pinned host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fj|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2301_10841_gb300 import datagen as G  # noqa: E402
+
+METRIC = "tuples/sec (in+out), star join, plain converted-binary Free Join plan"
+UNIT = "tuples/s"
+DIMS = G.STAR_DIMS
+N_FACT = 10_000_000
+THETA = G.STAR_THETA
+MIN_VARS = [4, 5, 6, 7]
+L2_FLUSH_BYTES = 256 << 20
+RESULT_D2H_BYTES = 8 + 4 * 32 + 8 + 4 + 4 + 8 * 16  # the library's result block
+
+
+def workload_config(n_fact=N_FACT):
+    return {
+        "workload": f"star join: F {n_fact} rows x 4 int32 FK Zipf(1.1) via seeded permutation; "
+                    f"D1..D4 = {'/'.join(str(d) for d in DIMS)} rows (int32 key, int32 attr "
+                    f"uniform [0,1e9)), selection attr < 1e8; COUNT(*) + MIN(a1..a4)",
+        "plan": "factor(binary2fj([F,D1,D2,D3,D4])), static cover, batch 2048",
+        "seed": 2,
+        "l2": "flushed between steps (256 MB write)",
+        "in_tuples": n_fact + sum(DIMS),
+    }
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes of the probe phase (the dominant kernel).
+# ---------------------------------------------------------------------------
+
+def probe_phase_bytes(fact, dims, theta):
+    """Compulsory HBM bytes of node 0 of the factored star plan: every 32-byte
+    sector of a fact column that holds a row the plan must read (k1 for all
+    rows; k_i only for rows that survived the probes of D1..D(i-1)), 16 bytes
+    per distinct dimension key probed (one hash slot each), and the 4-byte
+    per-survivor reads of the tail (vector length, offset and attribute).
+    Computed from the data by a host pass; the same model is stated in
+    the design doc."""
+    n = len(fact["cols"][0])
+    alive = np.ones(n, dtype=bool)
+    total = 0
+    for i, (fk, d) in enumerate(zip(fact["cols"], dims)):
+        rows = np.nonzero(alive)[0]
+        total += 32 * len(np.unique(rows >> 3))  # sectors of column k_i read
+        keys = fk[rows]
+        total += 16 * len(np.unique(keys))       # hash slots probed
+        key, attr = d["cols"]
+        passing = np.zeros(len(key) + 1, dtype=bool)
+        passing[key[attr < theta]] = True
+        hit = passing[np.clip(keys, 0, len(key))]
+        alive[rows[~hit]] = False
+    survivors = int(alive.sum())
+    total += survivors * 4 * 4 * 3  # per tail atom: count, begin, perm -> attr
+    return total, survivors
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("fj_kernels.cuh", "fj_exec.cuh", "fj_scan.cuh", "fj_internal.h"):
+        with open(os.path.join(ROOT, "paper_2301_10841_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_hash):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "star_expand_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if t.get("source_hash") == kernel_hash:
+            return t.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (the oracle) -- the only place bench.py runs oracle/.
+# ---------------------------------------------------------------------------
+
+def oracle_sample(fact, dims, budget_s=12.0, start_rows=250_000):
+    """Time the oracle's left-deep hash join on a prefix of F (full
+    dimensions), growing the prefix until one run takes a few seconds, and
+    scale repetitions to about `budget_s` of CPU work."""
+    import oracle
+    oracle.build()
+    n = start_rows
+    while True:
+        q = G.star_query({"name": "F", "cols": [c[:n] for c in fact["cols"]]}, dims, theta=THETA)
+        t0 = time.perf_counter()
+        cnt, mins, _ = oracle.binary_join(q, min_vars=MIN_VARS)
+        dt = time.perf_counter() - t0
+        if dt > 2.0 or n >= len(fact["cols"][0]):
+            break
+        n = min(len(fact["cols"][0]), n * 4)
+    reps = max(1, int(budget_s / max(dt, 1e-3)))
+    times = [dt]
+    for _ in range(reps - 1):
+        t0 = time.perf_counter()
+        oracle.binary_join(q, min_vars=MIN_VARS)
+        times.append(time.perf_counter() - t0)
+    tin = n + sum(len(d["cols"][0]) for d in dims)
+    tps = (tin + cnt) / statistics.median(times)
+    return {"value": tps, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"hash binary join (oracle O1, single thread) on the first {n} fact rows "
+                      f"with full dimensions, median of {len(times)} runs",
+            "seconds": sum(times)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle on the host cores, a bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    fact, dims = G.star_schema(n_fact=N_FACT, dims=DIMS, s=1.1, seed=2)
+    n = 1_000_000
+    q = G.star_query({"name": "F", "cols": [c[:n] for c in fact["cols"]]}, dims, theta=THETA)
+    tin = n + sum(DIMS)
+    for _ in range(args.warmup):
+        oracle.binary_join(q, min_vars=MIN_VARS)
+    times, cnt = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cnt, _, _ = oracle.binary_join(q, min_vars=MIN_VARS)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = (tin + cnt) / (ms / 1000)
+    sample = (f"hash binary join (oracle O1, single thread) on the first {n} of {N_FACT} fact "
+              f"rows with full dimensions, per step")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic", "config": workload_config(), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# The CUDA path.
+# ---------------------------------------------------------------------------
+
+def run_fj(args, rank, world):
+    import torch
+
+    from paper_2301_10841_gb300 import fj
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fact, dims = G.star_schema(n_fact=args.n_fact, dims=DIMS, s=1.1, seed=2)
+    rel_np = [fact] + dims
+    ctx = fj.Context(local)
+    dcols = {r["name"]: [torch.from_numpy(c).to(dev) for c in r["cols"]] for r in rel_np}
+    rels = {name: ctx.relation(cols, name) for name, cols in dcols.items()}
+    q = G.star_query(fact, dims, theta=THETA)
+    atoms = [{"rel": rels[a["rel"]["name"]], "vars": a["vars"], "preds": a["preds"]} for a in q]
+    plan = fj.binary_to_free_plan(atoms, [0, 1, 2, 3, 4], factor=True)
+    prep = fj.Prepared(ctx, atoms, plan, out_mode="count_min", min_vars=MIN_VARS,
+                       batch_size=args.batch, flags=fj.FLAG_TIMING)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        prep.reset()
+        prep.execute_async()
+
+    for _ in range(args.warmup):
+        step()
+        ref = prep.result()
+    expect = (ref.count, ref.mins)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, expand_ns, expand_n, kernels = [], 0, 0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        res = prep.result()
+        torch.cuda.synchronize()
+        if (res.count, res.mins) != expect:
+            raise SystemExit(f"result changed between steps: {(res.count, res.mins)} vs {expect}")
+        times.append(e0.elapsed_time(e1))
+        expand_ns += res.counters["expand_ns"]
+        expand_n += res.counters["expand_launches"]
+        kernels += res.counters["kernels"]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    in_tuples = args.n_fact + sum(DIMS)
+    per_rank = in_tuples + expect[0]
+    value = per_rank * world / (ms / 1000)
+
+    # End to end through the public API from pinned host buffers.
+    e2e = None
+    if not args.no_e2e:
+        pinned = {name: [torch.from_numpy(c).pin_memory() for c in r["cols"]]
+                  for name, r in ((r["name"], r) for r in rel_np)}
+        h2d = sum(c.numel() * 4 for cols in pinned.values() for c in cols)
+
+        def e2e_step():
+            hr = {name: ctx.relation_host(cols, name) for name, cols in pinned.items()}
+            at = [{"rel": hr[a["rel"]["name"]], "vars": a["vars"], "preds": a["preds"]} for a in q]
+            r = fj.execute(ctx, at, plan, out_mode="count_min", min_vars=MIN_VARS,
+                           batch_size=args.batch)
+            for h in hr.values():
+                h.release()
+            return r
+
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        torch.cuda.synchronize()
+        wall = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = e2e_step()
+            wall.append(time.perf_counter() - t0)
+            if (r.count, r.mins) != expect:
+                raise SystemExit("e2e result differs from the device-resident run")
+        e2e = {"value": per_rank * world / statistics.mean(wall), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": RESULT_D2H_BYTES,
+               "ms_per_step": 1000 * statistics.mean(wall)}
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    alg, survivors = probe_phase_bytes(fact, dims, THETA)
+    launch_s = expand_ns / max(1, expand_n) / 1e9
+    achieved = alg / launch_s / 1e9 if launch_s > 0 else None
+    khash = source_hash()
+    roofline = {"bound": "hbm", "kernel": "k_expand (node 0 probe phase)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
+                "traffic": profiled_traffic(khash), "algorithmic_bytes": alg,
+                "launch_us": launch_s * 1e6, "kernel_source": khash}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_sample(fact, dims)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic", "config": workload_config(args.n_fact),
+            "result": {"count": expect[0], "mins": expect[1], "survivors": survivors},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "counters": res.counters,
+            "gpu_launches": kernels, "impl": "fj"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fj", choices=["fj", "reference"])
+    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--n-fact", type=int, default=N_FACT)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_fj(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -229,6 +229,9 @@ fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
                                   ("simple trie", paper Section 5.3) */
 #define FJ_FLAG_EAGER_ROOT 2u  /* force every root level before the join
                                   ("simple lazy trie", Section 5.3) */
+#define FJ_FLAG_TIMING 4u      /* record CUDA events around the library's
+                                  kernels (on the context's stream) and report
+                                  device times in the FJ_CTR_*_NS counters */
 
 typedef struct {
   uint32_t batch_size;   /* cover tuples per vectorized batch (Fig. 11);
@@ -255,6 +258,10 @@ typedef struct {
 #define FJ_CTR_CHUNKS 7         /* expansion chunks launched */
 #define FJ_CTR_KERNELS 8        /* kernels launched by this execution */
 #define FJ_CTR_ATOM_BUILT_MASK 9  /* bit a set: atom a's root level was built */
+#define FJ_CTR_EXPAND_NS 10     /* FJ_FLAG_TIMING: device time in k_expand */
+#define FJ_CTR_EXPAND_LAUNCHES 11 /* FJ_FLAG_TIMING: k_expand launches timed */
+#define FJ_CTR_BUILD_NS 12      /* FJ_FLAG_TIMING: device time forcing COLT */
+#define FJ_CTR_SPAN_NS 13       /* FJ_FLAG_TIMING: first to last kernel */
 
 typedef struct {
   uint64_t count;                  /* COUNT(*) over the bag result */
@@ -299,6 +306,14 @@ fj_status fj_prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* plan,
                      const fj_exec_opts* opts, fj_prepared** out);
 fj_status fj_build_colt_level(fj_prepared* prep, int atom, int level);
 fj_status fj_execute_prepared(fj_prepared* prep, fj_result* out);
+/* Enqueue an execution without waiting for it: returns once every kernel is
+ * enqueued (plans whose later nodes need a host-side size read still wait for
+ * those reads).  fj_prepared_result then synchronizes and fills *out.  The
+ * pair is equivalent to fj_execute_prepared, except that a materialized
+ * output larger than the prepared buffer fails with FJ_ERR_OUTPUT_OVERFLOW
+ * instead of being retried. */
+fj_status fj_execute_prepared_async(fj_prepared* prep);
+fj_status fj_prepared_result(fj_prepared* prep, fj_result* out);
 fj_status fj_reset_prepared(fj_prepared* prep);
 void fj_prepared_free(fj_prepared* prep);
 

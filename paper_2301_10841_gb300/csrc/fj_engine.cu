@@ -22,7 +22,7 @@
 #include <string>
 #include <vector>
 
-#include "fj_exec.cuh"
+#include "fj_scan.cuh"
 #include "fj_plan.h"
 
 using namespace fj;
@@ -154,13 +154,39 @@ struct fj_prepared {
   int2* d_level_jobs = nullptr;            // [atom][level] single jobs
   std::vector<uint32_t> max_rows_job;      // per node: largest atom among its jobs
   std::vector<uint32_t> max_req_job;
+  std::vector<bool> roots_only;            // per node: every force job is a root
   int32_t* d_out = nullptr;
   uint64_t out_cap = 0;
   bool materialize = false;
   size_t smem_expand = 0;
   int expand_blocks_per_sm = 1;
+  int expand_r = 8;
+  // Node 0 streamed from its cover's base table (k_scan_probe).
+  bool scan0 = false;
+  ScanDev sc0{};
+  int scan_r = 8;
+  size_t scan_smem = 0;
+  int scan_blocks_per_sm = 1;
   uint64_t kernels = 0;
   uint64_t chunks = 0;
+  bool explicit_built = false;  // levels built outside the join since reset
+  // FJ_FLAG_TIMING: event pool and the pairs recorded by this execution.
+  std::vector<cudaEvent_t> events;
+  size_t n_events = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_expand, t_build;
+  cudaEvent_t t_first = nullptr, t_last = nullptr;
+
+  bool timing() const { return opts.flags & FJ_FLAG_TIMING; }
+  cudaEvent_t mark() {
+    if (n_events == events.size()) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      events.push_back(e);
+    }
+    cudaEvent_t e = events[n_events++];
+    CK(cudaEventRecord(e, ctx->stream));
+    return e;
+  }
 
   template <typename T>
   T* alloc(size_t n) {
@@ -187,12 +213,15 @@ void run_scan(fj_prepared* P, Op op, int n_jobs, uint64_t ub_n) {
   P->kernels += 3;
 }
 
-// COLT forcing of a batch of (atom, level) jobs.
-void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uint32_t ub_req) {
+// COLT forcing of a batch of (atom, level) jobs.  `roots` says every job is
+// a root level (its single parent needs no row-offset or child-first scan).
+void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uint32_t ub_req,
+           bool roots) {
   if (n_jobs == 0) return;
   fj_ctx* c = P->ctx;
   cudaStream_t s = c->stream;
   ForceJobs fj{P->d_atoms, d_jobs, n_jobs};
+  cudaEvent_t t0 = P->timing() ? P->mark() : nullptr;
   int cap = c->n_sm * 8;
   int g_rows = blocks_for(ub_rows, kThreads * 4, cap);
   int g_ht = blocks_for(uint64_t(ub_rows) * 2 + 2, kThreads * 4, cap);
@@ -201,20 +230,75 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
   k_force_clear<<<dim3(g_ht, n_jobs), kThreads, 0, s>>>(fj);
   CK_LAUNCH("force prepare");
   P->kernels += 3;
-  run_scan<uint32_t>(P, RowOffOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
+  if (!roots) run_scan<uint32_t>(P, RowOffOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
   k_force_insert<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, c->d_res);
   CK_LAUNCH("force insert");
   P->kernels += 1;
-  run_scan<uint32_t>(P, ChildFirstOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
+  if (!roots) run_scan<uint32_t>(P, ChildFirstOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
   k_force_assign<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
-  P->kernels += 1;
-  run_scan<uint32_t>(P, EntryPosOp{P->d_atoms, d_jobs}, n_jobs, ub_rows);
-  k_force_begin<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
   k_force_scatter<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
   k_force_finish<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, c->d_res);
   k_force_reset_req<<<n_jobs, 32, 0, s>>>(fj);
   CK_LAUNCH("force finish");
-  P->kernels += 5;
+  P->kernels += 4;
+  if (t0) P->t_build.emplace_back(t0, P->mark());
+}
+
+template <int R>
+void launch_expand_r(fj_prepared* P, int grid, const NodeDev& nd) {
+  fj_ctx* c = P->ctx;
+  if (nd.dynamic)
+    k_expand<R><<<grid, kThreads, P->smem_expand, c->stream>>>(nd, P->d_atoms, c->d_res);
+  else
+    k_expand_static<R><<<grid, kThreads, P->smem_expand, c->stream>>>(nd, P->d_atoms, c->d_res);
+}
+
+template <int R>
+void expand_attrs(size_t smem, int* blocks) {
+  const void* fns[2] = {reinterpret_cast<const void*>(&k_expand<R>),
+                        reinterpret_cast<const void*>(&k_expand_static<R>)};
+  *blocks = 1 << 20;
+  for (const void* fn : fns) {
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int b = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, smem));
+    *blocks = std::min(*blocks, std::max(1, b));
+  }
+}
+
+void expand_setup(int r, size_t smem, int* blocks) {
+  switch (r) {
+    case 1: expand_attrs<1>(smem, blocks); break;
+    case 2: expand_attrs<2>(smem, blocks); break;
+    case 4: expand_attrs<4>(smem, blocks); break;
+    case 8: expand_attrs<8>(smem, blocks); break;
+    default: expand_attrs<16>(smem, blocks); break;
+  }
+}
+
+constexpr int kScanR = 8;  // rows per lane per warp tile of the scan kernel
+
+void scan_attrs(size_t smem, int* blocks) {
+  const void* fn = reinterpret_cast<const void*>(&k_scan_probe<kScanR>);
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, smem));
+  if (*blocks < 1) *blocks = 1;
+}
+
+void launch_scan(fj_prepared* P, int grid, const NodeDev& nd) {
+  fj_ctx* c = P->ctx;
+  k_scan_probe<kScanR><<<grid, kThreads, P->scan_smem, c->stream>>>(nd, P->sc0, P->d_atoms,
+                                                                    c->d_res);
+}
+
+void launch_expand(fj_prepared* P, int grid, const NodeDev& nd) {
+  switch (P->expand_r) {
+    case 1: launch_expand_r<1>(P, grid, nd); break;
+    case 2: launch_expand_r<2>(P, grid, nd); break;
+    case 4: launch_expand_r<4>(P, grid, nd); break;
+    case 8: launch_expand_r<8>(P, grid, nd); break;
+    default: launch_expand_r<16>(P, grid, nd); break;
+  }
 }
 
 void sync_read_total(fj_prepared* P, const uint64_t* d_total, uint64_t* out) {
@@ -232,15 +316,26 @@ void run_node(fj_prepared* P, int k, uint64_t ub_items) {
   k_choose<<<g_items, kThreads, 0, s>>>(nd, P->d_atoms);
   CK_LAUNCH("choose");
   P->kernels += 1;
-  force(P, P->d_jobs[k], int(P->jobs[k].size()), P->max_rows_job[k], P->max_req_job[k]);
-  k_fanout<<<g_items, kThreads, 0, s>>>(nd, P->d_atoms);
-  CK_LAUNCH("fanout");
-  P->kernels += 1;
-  run_scan<uint64_t>(P,
-                     FanScanOp{nd.fan, nd.scan, nd.total, nd.n_items, nd.single_item},
-                     1, ub_items);
+  force(P, P->d_jobs[k], int(P->jobs[k].size()), P->max_rows_job[k], P->max_req_job[k],
+        P->roots_only[k]);
   uint64_t total = 0;
-  sync_read_total(P, nd.total, &total);
+  const SubDev& S0 = nd.sub[0];
+  bool use_scan = k == 0 && P->scan0;
+  bool host_known = use_scan || (k == 0 && !nd.dynamic && S0.last && S0.lvl == 0 &&
+                                 !(P->opts.flags & (FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT)) &&
+                                 !P->explicit_built);
+  if (host_known) {
+    // The single root tuple iterates the cover's base table directly.
+    total = P->host_atoms[S0.atom].n_rows;
+  } else {
+    k_fanout<<<g_items, kThreads, 0, s>>>(nd, P->d_atoms);
+    CK_LAUNCH("fanout");
+    P->kernels += 1;
+    run_scan<uint64_t>(P,
+                       FanScanOp{nd.fan, nd.scan, nd.total, nd.n_items, nd.single_item},
+                       1, ub_items);
+    sync_read_total(P, nd.total, &total);
+  }
   if (total == 0) return;
   bool items_mode = nd.mode == kModeItems;
   uint64_t step = items_mode ? P->items[k + 1].cap : total;
@@ -248,9 +343,16 @@ void run_node(fj_prepared* P, int k, uint64_t ub_items) {
     nd.chunk_begin = c0;
     nd.chunk_end = std::min(total, c0 + step);
     if (items_mode) CK(cudaMemsetAsync(P->items[k + 1].n, 0, sizeof(uint32_t), s));
-    int grid = blocks_for(nd.chunk_end - c0, nd.tile, c->n_sm * P->expand_blocks_per_sm);
-    k_expand<<<grid, kThreads, P->smem_expand, s>>>(nd, P->d_atoms, c->d_res);
+    cudaEvent_t t0 = P->timing() ? P->mark() : nullptr;
+    if (use_scan) {
+      int grid = blocks_for(nd.chunk_end - c0, P->scan_r * kThreads, c->n_sm * P->scan_blocks_per_sm);
+      launch_scan(P, grid, nd);
+    } else {
+      int grid = blocks_for(nd.chunk_end - c0, nd.tile, c->n_sm * P->expand_blocks_per_sm);
+      launch_expand(P, grid, nd);
+    }
     CK_LAUNCH("expand");
+    if (t0) P->t_expand.emplace_back(t0, P->mark());
     P->kernels += 1;
     P->chunks += 1;
     if (items_mode) run_node(P, k + 1, nd.chunk_end - c0);
@@ -349,6 +451,7 @@ static void compile(fj_prepared* P) {
     R.child_state = P->alloc<uint32_t>(1);
     R.child_first = P->alloc<uint32_t>(1);
     R.child_nkeys = P->alloc<uint32_t>(1);
+    R.fill = P->alloc<uint32_t>(1);
     R.entries_cap = 1;
     for (int l = 1; l <= A.n_levels; ++l) {
       LevelDev& L = D.L[l];
@@ -367,6 +470,13 @@ static void compile(fj_prepared* P) {
       L.key = P->alloc<uint64_t>(n);
       L.ht_cap_max = pow2_at_least(uint64_t(double(n) / load) + 1);
       L.ht = P->alloc<uint4>((size_t(L.ht_cap_max) + 1) * (L.wide ? 2 : 1));
+      if (!L.wide) {
+        // Bloom filter: about 8 bits per row, 256 B to 32 KB.
+        uint32_t words = 64;
+        while (words < 8192 && uint64_t(words) * 32 < uint64_t(n) * 8) words <<= 1;
+        L.filter_words = words;
+        L.filter = P->alloc<uint32_t>(words);
+      }
       L.req_cap = D.L[l - 1].entries_cap;
       L.req = P->alloc<uint32_t>(L.req_cap);
       L.rowoff = P->alloc<uint32_t>(size_t(L.req_cap) + 1);
@@ -414,28 +524,25 @@ static void compile(fj_prepared* P) {
     }
   }
 
-  // Batch tile and shared memory.
+  // Batch tile (R batch elements per thread) and shared memory.
   uint32_t tile = o.batch_size ? o.batch_size : 2048;
-  uint32_t t2 = 256;
-  while (t2 < tile && t2 < 4096) t2 <<= 1;
-  tile = t2;
+  int R = 1;
+  while (R < 16 && uint32_t(R * kThreads) < tile) R <<= 1;
   int max_sub = 1;
   for (int k = 0; k < nn; ++k) max_sub = std::max<int>(max_sub, int(plan[k].size()));
-  auto smem_for = [&](uint32_t t) {
-    return size_t(t) * (8 + 4 + 4 + 4 * max_sub + 2 + 2);
-  };
-  while (tile > 256 && smem_for(tile) > 160 * 1024) tile >>= 1;
-  P->smem_expand = smem_for(tile);
-  CK(cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          int(P->smem_expand)));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P->expand_blocks_per_sm, k_expand, kThreads,
-                                                   P->smem_expand));
-  if (P->expand_blocks_per_sm < 1) P->expand_blocks_per_sm = 1;
+  // Static kernel: mult, item, element, per-subatom handles, two lists.
+  auto smem_for = [&](int r) { return size_t(r) * kThreads * (8 + 4 + 4 + 4 * max_sub + 4); };
+  while (R > 1 && smem_for(R) > 160 * 1024) R >>= 1;
+  P->expand_r = R;
+  P->smem_expand = smem_for(R);
+  tile = uint32_t(R * kThreads);
+  expand_setup(R, P->smem_expand, &P->expand_blocks_per_sm);
 
   // Item buffers.
   uint64_t max_rows = 1;
   for (fj_rel* r : P->rels) max_rows = std::max<uint64_t>(max_rows, r->n_rows);
   uint32_t cap = uint32_t(std::min<uint64_t>(1ull << 24, std::max<uint64_t>(1ull << 16, max_rows)));
+  cap &= ~4095u;  // chunks start on a 16-byte boundary of every column
   P->items.assign(nn + 1, ItemsBuf{});
   for (int k = 0; k <= P->last; ++k) {
     ItemsBuf& B = P->items[k];
@@ -471,6 +578,7 @@ static void compile(fj_prepared* P) {
   P->d_jobs.assign(nn, nullptr);
   P->max_rows_job.assign(nn, 1);
   P->max_req_job.assign(nn, 1);
+  P->roots_only.assign(nn, true);
   for (int k = 0; k <= P->last; ++k) {
     NodeDev& N = P->nd[k];
     std::memset(&N, 0, sizeof(N));
@@ -498,6 +606,7 @@ static void compile(fj_prepared* P) {
       S.is_cover = std::find(cov[k].begin(), cov[k].end(), s) != cov[k].end();
       if (P->ap[sa.atom].may_force[S.lvl + 1] && (dynamic[k] || s != 0 || !S.last)) {
         P->jobs[k].push_back(make_int2(sa.atom, S.lvl + 1));
+        if (S.lvl + 1 != 1) P->roots_only[k] = false;
         P->max_rows_job[k] = std::max<uint32_t>(P->max_rows_job[k], P->host_atoms[sa.atom].n_rows);
         P->max_req_job[k] =
             std::max<uint32_t>(P->max_req_job[k], P->host_atoms[sa.atom].L[S.lvl].entries_cap);
@@ -601,6 +710,118 @@ static void upload_atoms(fj_prepared* P, const fj_query* query) {
                      cudaMemcpyHostToDevice, c->stream));
 }
 
+// Resolve the static-cover fast path of every node: variable sources, the
+// cover's arrays and the probed hash levels (device addresses of the masks,
+// which kernels fill when the level is first forced).
+static void finalize_nodes(fj_prepared* P) {
+  const PPlan& plan = P->plan;
+  const PQuery& q = P->q;
+  for (int k = 0; k <= P->last; ++k) {
+    NodeDev& N = P->nd[k];
+    if (N.dynamic) continue;
+    const SubDev& C = N.sub[0];
+    const AtomDev& ca = P->host_atoms[C.atom];
+    const ItemsBuf& In = P->items[k];
+    for (int u = 0; u < FJ_MAX_VARS; ++u) {
+      VarSrc& v = N.src[u];
+      std::memset(&v, 0, sizeof(v));
+      v.kind = kSrcItem;
+      if ((N.avs_mask >> u) & 1u) {
+        v.col = In.var[u];
+        continue;
+      }
+      int j = N.vpos[0][u];
+      if (j < 0) continue;
+      if (C.last) {
+        v.kind = kSrcRow;
+        v.col = ca.cols[C.col[j]];
+      } else if (ca.L[C.lvl + 1].wide) {
+        v.kind = kSrcKeyWide;
+        v.col = ca.cols[C.col[j]];
+        v.perm = ca.perm;
+        v.begin = ca.L[C.lvl + 1].begin;
+      } else {
+        v.kind = kSrcKey;
+        v.key = ca.L[C.lvl + 1].key;
+        v.nk = ca.L[C.lvl + 1].nk;
+        v.pos = j;
+      }
+    }
+    N.cover_root_mat = &P->d_atoms[C.atom].root_mat;
+    N.cover_perm = ca.perm;
+    N.cover_begin = ca.L[C.lvl].begin;
+    N.cover_first = ca.L[C.lvl].child_first;
+    N.cover_hsrc = C.lvl >= 1 ? In.h[C.atom] : nullptr;
+    N.n_probe = 0;
+    for (int s = 1; s < N.n_sub; ++s) {
+      const SubDev& S = N.sub[s];
+      const AtomDev& a = P->host_atoms[S.atom];
+      ProbeDev& Pd = N.probe[N.n_probe++];
+      Pd.sub = s;
+      Pd.nv = S.nv;
+      for (int j = 0; j < 3; ++j) Pd.var[j] = j < S.nv ? S.var[j] : 0;
+      Pd.ht = a.L[S.lvl + 1].ht;
+      Pd.mask = &P->d_atoms[S.atom].L[S.lvl + 1].mask;
+      Pd.filter = a.L[S.lvl + 1].filter;
+      Pd.filter_words = a.L[S.lvl + 1].filter_words;
+      Pd.filter_on = &P->d_atoms[S.atom].L[S.lvl + 1].filter_on;
+      Pd.nk = a.L[S.lvl + 1].nk;
+      Pd.wide = a.L[S.lvl + 1].wide;
+      Pd.last = S.last;
+      Pd.hsrc = S.lvl >= 1 ? In.h[S.atom] : nullptr;
+    }
+    (void)plan;
+    (void)q;
+  }
+}
+
+// Node 0 iterates its cover's base table: resolve every probe's key columns
+// (all from the cover row) and the cover's predicates for k_scan_probe.
+static void setup_scan(fj_prepared* P) {
+  P->scan0 = false;
+  NodeDev& N = P->nd[0];
+  const SubDev& C = N.sub[0];
+  if (N.dynamic || !C.last || C.lvl != 0) return;
+  const AtomDev& ca = P->host_atoms[C.atom];
+  ScanDev sc{};
+  sc.n_probe = N.n_probe;
+  for (int p = 0; p < N.n_probe; ++p) {
+    const ProbeDev& Pd = N.probe[p];
+    ScanProbe& S = sc.probe[p];
+    S.nk = Pd.nv;
+    for (int j = 0; j < Pd.nv && j < 3; ++j) {
+      const VarSrc& v = N.src[Pd.var[j]];
+      if (v.kind != kSrcRow) return;
+      S.kcol[j] = v.col;
+    }
+    S.wide = Pd.wide;
+    S.last = Pd.last;
+    S.sub = Pd.sub;
+    S.ht = Pd.ht;
+    S.mask = Pd.mask;
+    S.filter = Pd.filter;
+    S.filter_words = Pd.filter_words;
+    S.filter_on = Pd.filter_on;
+  }
+  if (sc.n_probe > 0) {
+    const ScanProbe& F = sc.probe[0];
+    sc.k1 = F.nk == 1 && !F.wide && !F.last;
+    sc.vec_ok = sc.k1 && !(reinterpret_cast<uintptr_t>(F.kcol[0]) & 15);
+  }
+  sc.n_preds = ca.n_preds;
+  for (int p = 0; p < ca.n_preds; ++p) {
+    sc.pred_col[p] = ca.cols[ca.pred_col[p]];
+    sc.pred_op[p] = ca.pred_op[p];
+    sc.pred_val[p] = ca.pred_val[p];
+  }
+  for (int p = 0; p < sc.n_probe; ++p) sc.track |= sc.probe[p].last;
+  P->scan_r = kScanR;
+  P->scan_smem = size_t(kThreads / 32) * scan_queue_bytes(N.n_probe, sc.track);
+  scan_attrs(P->scan_smem, &P->scan_blocks_per_sm);
+  P->sc0 = sc;
+  P->scan0 = true;
+}
+
 static void ensure_output(fj_prepared* P, uint64_t rows) {
   if (!P->materialize) return;
   int nh = int(P->q.head.size());
@@ -629,7 +850,7 @@ static void build_level(fj_prepared* P, int atom, int l) {
   CK_LAUNCH("request_all");
   P->kernels += 1;
   force(P, P->d_level_jobs + size_t(atom) * kMaxLevels + l, 1, P->host_atoms[atom].n_rows,
-        P->host_atoms[atom].L[l - 1].entries_cap);
+        P->host_atoms[atom].L[l - 1].entries_cap, l == 1);
 }
 
 static void eager_builds(fj_prepared* P) {
@@ -645,8 +866,16 @@ static void eager_builds(fj_prepared* P) {
 }
 
 static void run_once(fj_prepared* P) {
+  if (P->timing()) P->t_first = P->mark();
   eager_builds(P);
   run_node(P, 0, 1);
+  if (P->timing()) P->t_last = P->mark();
+}
+
+static uint64_t elapsed_ns(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  return uint64_t(double(ms) * 1e6);
 }
 
 static void read_result(fj_prepared* P, fj_result* out, bool* retry) {
@@ -682,12 +911,29 @@ static void read_result(fj_prepared* P, fj_result* out, bool* retry) {
   for (int i = 0; i < 16; ++i) out->counters[i] = r.ctr[i];
   out->counters[FJ_CTR_CHUNKS] = P->chunks;
   out->counters[FJ_CTR_KERNELS] = P->kernels;
+  if (P->timing() && P->t_first) {
+    uint64_t ex = 0, bu = 0;
+    for (auto& pr : P->t_expand) ex += elapsed_ns(pr.first, pr.second);
+    for (auto& pr : P->t_build) bu += elapsed_ns(pr.first, pr.second);
+    out->counters[FJ_CTR_EXPAND_NS] = ex;
+    out->counters[FJ_CTR_EXPAND_LAUNCHES] = P->t_expand.size();
+    out->counters[FJ_CTR_BUILD_NS] = bu;
+    out->counters[FJ_CTR_SPAN_NS] = elapsed_ns(P->t_first, P->t_last);
+  }
+}
+
+static void begin_execution(fj_prepared* P) {
+  P->kernels = 0;
+  P->chunks = 0;
+  P->n_events = 0;
+  P->t_expand.clear();
+  P->t_build.clear();
+  P->t_first = P->t_last = nullptr;
 }
 
 static void execute(fj_prepared* P, fj_result* out) {
   for (int attempt = 0; attempt < 3; ++attempt) {
-    P->kernels = 0;
-    P->chunks = 0;
+    begin_execution(P);
     if (P->materialize) {
       uint64_t want = P->opts.list_limit ? P->opts.list_limit : (P->out_cap ? P->out_cap : 1u << 20);
       ensure_output(P, want);
@@ -708,8 +954,24 @@ static void execute(fj_prepared* P, fj_result* out) {
   fail(FJ_ERR_CUDA, "internal: output sizing did not converge");
 }
 
+static void execute_async(fj_prepared* P) {
+  begin_execution(P);
+  if (P->materialize)
+    ensure_output(P, P->opts.list_limit ? P->opts.list_limit : (P->out_cap ? P->out_cap : 1u << 20));
+  reset_state(P, false);
+  run_once(P);
+}
+
+static void prepared_result(fj_prepared* P, fj_result* out) {
+  bool retry = false;
+  read_result(P, out, &retry);
+  if (retry || (P->materialize && P->opts.list_limit && out->count > P->opts.list_limit))
+    fail(FJ_ERR_OUTPUT_OVERFLOW, "more output rows than the prepared output buffer");
+}
+
 static void prepared_release(fj_prepared* P) {
   if (!P) return;
+  for (cudaEvent_t e : P->events) cudaEventDestroy(e);
   for (void* p : P->allocs) dfree(P->ctx, p);
   if (P->d_out) dfree(P->ctx, P->d_out);
   cudaStreamSynchronize(P->ctx->stream);
@@ -751,6 +1013,8 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
   try {
     compile(P.get());
     upload_atoms(P.get(), query);
+    finalize_nodes(P.get());
+    setup_scan(P.get());
     reset_state(P.get(), true);
   } catch (...) {
     for (void* p : P->allocs) dfree(ctx, p);
@@ -888,6 +1152,21 @@ fj_status fj_build_colt_level(fj_prepared* P, int atom, int level) {
            "fj_build_colt_level: this level is only iterated under the plan and opts; prepare "
            "with FJ_FLAG_EAGER_ALL to build every level");
     build_level(P, atom, l);
+    P->explicit_built = true;
+  });
+}
+
+fj_status fj_execute_prepared_async(fj_prepared* P) {
+  return guarded([&] {
+    if (!P) fail(FJ_ERR_INVALID_ARG, "NULL prepared plan");
+    execute_async(P);
+  });
+}
+
+fj_status fj_prepared_result(fj_prepared* P, fj_result* out) {
+  return guarded([&] {
+    if (!P || !out) fail(FJ_ERR_INVALID_ARG, "NULL argument");
+    prepared_result(P, out);
   });
 }
 
@@ -902,6 +1181,7 @@ fj_status fj_reset_prepared(fj_prepared* P) {
   return guarded([&] {
     if (!P) fail(FJ_ERR_INVALID_ARG, "NULL prepared plan");
     reset_state(P, true);
+    P->explicit_built = false;
   });
 }
 

@@ -53,6 +53,12 @@ struct LevelDev {
   // Key columns: indices into AtomDev::cols (0 to 3 of them).
   int nk = 0;
   int kcol[3] = {0, 0, 0};
+  // Blocked Bloom filter over this level's keys (narrow levels): one 32-bit
+  // word per key hash, two bits set.  Probes test it before touching the
+  // table; it is switched off on the device when the level holds too many
+  // keys for its size.
+  uint32_t* filter = nullptr;
+  uint32_t filter_words = 0;  // power of two
   // Wide levels (more than one key value below the root, or three values)
   // use 32-byte slots {parent, k0, k1, k2 | entry, count, -, -} claimed with
   // a 16-byte compare-and-swap; their entries keep only the parent in key[]
@@ -73,6 +79,8 @@ struct LevelDev {
   uint32_t base;       // first entry id of the current force
   uint32_t pos_total;  // offsets placed by the current force
   uint32_t n_in;       // rows that reach this level's table (sizing)
+  uint32_t filter_on;  // the filter is built and selective
+  uint32_t n_tmp;      // (row, slot) pairs staged by the current force
 };
 
 struct AtomDev {
@@ -121,6 +129,39 @@ struct TailDev {
   int min_col[FJ_MAX_ARITY];  // column index into AtomDev::cols
 };
 
+// Where one variable's value comes from for a batch element of a node whose
+// cover is fixed (static): the input tuples (by item), a base-table column
+// of the cover (by row), or the cover's map key (by entry).
+constexpr int kSrcItem = 0;
+constexpr int kSrcRow = 1;
+constexpr int kSrcKey = 2;      // narrow map level: unpack key[entry]
+constexpr int kSrcKeyWide = 3;  // wide map level: column at perm[begin[entry]]
+struct VarSrc {
+  int kind;
+  int pos;                  // position in the key (kSrcKey)
+  int nk;                   // key arity (kSrcKey)
+  const int32_t* col;       // kSrcItem: input array; kSrcRow/kSrcKeyWide: column
+  const uint64_t* key;      // kSrcKey
+  const uint32_t* perm;     // kSrcKeyWide
+  const uint32_t* begin;    // kSrcKeyWide
+};
+
+// One probe phase of a static-cover node, resolved on the host.
+struct ProbeDev {
+  int sub;                  // subatom index in the node
+  int nv;
+  int var[3];
+  const uint4* ht;
+  const uint32_t* mask;     // device-side table mask (read once per block)
+  const uint32_t* filter;   // Bloom filter words (null: none)
+  uint32_t filter_words;
+  const uint32_t* filter_on;  // device-side switch (read once per block)
+  int nk;
+  int wide;
+  int last;                 // ends its atom: multiply by the vector length
+  const uint32_t* hsrc;     // parent handles by item (null: the root)
+};
+
 constexpr int kModeItems = 0;
 constexpr int kModeAggregate = 1;
 constexpr int kModeMaterialize = 2;
@@ -132,6 +173,15 @@ struct NodeDev {
   SubDev sub[FJ_MAX_SUB];
   int8_t vpos[FJ_MAX_SUB][FJ_MAX_VARS];   // position of a variable in sub s
   uint32_t avs_mask;                      // bit v: variable v bound before
+  // Static-cover fast path (dynamic == 0): resolved sources and probes.
+  VarSrc src[FJ_MAX_VARS];
+  int n_probe;
+  ProbeDev probe[FJ_MAX_SUB];
+  const uint32_t* cover_root_mat;         // &atoms[cover].root_mat
+  const uint32_t* cover_perm;
+  const uint32_t* cover_begin;            // L[lvl].begin of the cover
+  const uint32_t* cover_first;            // L[lvl].child_first of the cover
+  const uint32_t* cover_hsrc;             // cover parent handles by item
   // Input partial tuples (structure of arrays).
   const int32_t* in_var[FJ_MAX_VARS];     // by variable id
   const uint32_t* in_h[FJ_MAX_ATOMS];     // by atom

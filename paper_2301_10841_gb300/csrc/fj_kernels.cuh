@@ -33,6 +33,33 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   return k;
 }
 
+// 32-bit finalizer of MurmurHash3 (Austin Appleby, public domain).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Hash of a narrow key word (parent entry in the high half).
+__device__ __forceinline__ uint32_t hash_key(uint64_t kw) {
+  return fmix32(uint32_t(kw) ^ fmix32(uint32_t(kw >> 32) + 0x9e3779b9u));
+}
+
+// Blocked Bloom filter: word (h mod words), bits 13..17 and 18..22 of h.
+__device__ __forceinline__ uint32_t bloom_bits(uint32_t h) {
+  return (1u << ((h >> 13) & 31u)) | (1u << ((h >> 18) & 31u));
+}
+
+// True when the filter rules the key out (no false negatives).
+__device__ __forceinline__ bool bloom_rejects(const uint32_t* __restrict__ f, uint32_t words,
+                                              uint32_t h) {
+  uint32_t m = bloom_bits(h);
+  return (__ldg(&f[h & (words - 1)]) & m) != m;
+}
+
 // Key word of (parent, key tuple).  One level's keys all have the same arity:
 // 0 or 1 values are packed beside the parent; 2 values fill the word and are
 // only used where the parent is the single root entry.
@@ -91,7 +118,7 @@ __device__ __forceinline__ uint32_t ht_insert(uint4* ht, uint32_t mask, uint64_t
     claimed = atomicCAS(&ht[s].z, kNone, 0u) == kNone;
     return s;
   }
-  uint32_t h = uint32_t(mix64(kw)) & mask;
+  uint32_t h = hash_key(kw) & mask;
   for (uint32_t it = 0; it <= mask; ++it) {
     unsigned long long* kp = slot_key(ht, h);
     unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(kp);
@@ -119,7 +146,7 @@ __device__ __forceinline__ bool ht_find(const uint4* __restrict__ ht, uint32_t m
     cnt = s.w;
     return s.w != 0;
   }
-  uint32_t h = uint32_t(mix64(kw)) & mask;
+  uint32_t h = hash_key(kw) & mask;
   for (uint32_t it = 0; it <= mask; ++it) {
     uint4 s = __ldg(&ht[h]);
     uint64_t k = (uint64_t(s.y) << 32) | s.x;
@@ -318,7 +345,16 @@ __global__ void __launch_bounds__(kThreads) k_force_count(ForceJobs fj) {
   int2 jb = fj.jobs[blockIdx.y];
   AtomDev& a = fj.atoms[jb.x];
   LevelDev& L = a.L[jb.y];
-  if (L.n_req == 0 || L.cleared) return;
+  if (L.n_req == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // Per-force counters (the parent scans below overwrite n_rows for
+    // non-root jobs).
+    L.n_new = 0;
+    L.n_tmp = 0;
+    L.base = L.n_entries;
+    if (job_identity(a, jb.y)) L.n_rows = a.n_rows;
+  }
+  if (L.cleared) return;
   if (!job_identity(a, jb.y)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) L.n_in = a.n_pass;
     return;
@@ -345,6 +381,8 @@ __global__ void k_force_prepare(ForceJobs fj) {
   uint32_t cap = 16;
   while (float(cap) < want && cap < L.ht_cap_max) cap <<= 1;
   L.mask = cap - 1;
+  // Keep the filter only with at least 4 bits per key.
+  L.filter_on = L.filter && uint64_t(L.n_in) * 4 <= uint64_t(L.filter_words) * 32;
 }
 
 // Pass 1: clear a level's table the first time it is forced.
@@ -354,6 +392,10 @@ __global__ void k_force_clear(ForceJobs fj) {
   LevelDev& L = a.L[jb.y];
   if (L.n_req == 0 || L.cleared) return;
   uint32_t n = L.mask + 2;
+  if (L.filter_on)
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < L.filter_words;
+         i += gridDim.x * blockDim.x)
+      L.filter[i] = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (L.wide) {
       L.ht[2 * size_t(i)] = make_uint4(kNone, kNone, kNone, kNone);
@@ -388,8 +430,6 @@ struct RowOffOp {
     LevelDev& L = atoms[jb.x].L[jb.y];
     L.n_rows = v;
     L.rowoff[L.n_req] = v;
-    L.n_new = 0;
-    L.base = L.n_entries;
   }
 };
 
@@ -404,7 +444,10 @@ __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t 
   return lo;
 }
 
-// Pass 2: insert every row's (parent, key) and count it.
+// Pass 2: insert every row's (parent, key) and count it.  Each block walks
+// its rows 256 at a time; the counters every row group appends to (new
+// slots, staged rows, and the root's key count) are summed per block in
+// shared memory and advanced with one global atomic per counter.
 __global__ void __launch_bounds__(kThreads) k_force_insert(ForceJobs fj, ResultDev* res) {
   int2 jb = fj.jobs[blockIdx.y];
   AtomDev& a = fj.atoms[jb.x];
@@ -412,18 +455,23 @@ __global__ void __launch_bounds__(kThreads) k_force_insert(ForceJobs fj, ResultD
   LevelDev& P = a.L[jb.y - 1];
   uint32_t nreq = L.n_req;
   if (nreq == 0) return;
-  uint32_t n = L.n_rows;
-  bool ident = job_identity(a, jb.y);
-  uint32_t mask = L.mask;
-  int nk = L.nk;
-  int wide = L.wide;
+  const uint32_t n = L.n_rows;
+  const bool ident = job_identity(a, jb.y);
+  const uint32_t mask = L.mask;
+  const int nk = L.nk;
+  const int wide = L.wide;
+  const bool fon = L.filter_on;
+  const bool root = jb.y == 1;  // single parent: entry 0 of the virtual level
   const int32_t* c0 = a.cols[L.kcol[0]];
   const int32_t* c1 = a.cols[L.kcol[1]];
   const int32_t* c2 = a.cols[L.kcol[2]];
-  uint32_t stride = gridDim.x * blockDim.x;
-  uint32_t start = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-  for (uint32_t base = start; base < n; base += stride) {
-    uint32_t t = base + lane_id();
+  __shared__ uint32_t s_cnt[3];   // claimed (new slots), staged rows, -
+  __shared__ uint32_t s_base[3];
+  const uint32_t warp = threadIdx.x >> 5;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t t = base + threadIdx.x;
     bool active = t < n;
     uint32_t row = 0, parent = 0, slot = kNone;
     bool claimed = false;
@@ -445,35 +493,55 @@ __global__ void __launch_bounds__(kThreads) k_force_insert(ForceJobs fj, ResultD
       } else {
         uint64_t kw = pack_key(parent, nk, nk > 0 ? c0[row] : 0, nk > 1 ? c1[row] : 0);
         slot = ht_insert(L.ht, mask, kw, claimed, &res->status);
+        if (claimed && fon) {
+          uint32_t h = hash_key(kw);
+          atomicOr(&L.filter[h & (L.filter_words - 1)], bloom_bits(h));
+        }
       }
       if (slot == kNone) active = false;
     }
-    // Claimed slots: one local index per parent (grouped per warp), and an
-    // append to the new-slot list.
+    if (active) atomicAdd(slot_cnt(L.ht, wide, slot), 1u);
+    // Per-warp ranks, per-block offsets.
     uint32_t cmask = __ballot_sync(0xffffffffu, claimed);
-    if (claimed) {
-      uint32_t grp = __match_any_sync(cmask, parent);
-      uint32_t leader = __ffs(grp) - 1;
-      uint32_t rank = __popc(grp & lanemask_lt());
-      uint32_t first = 0;
-      if (lane_id() == leader) first = atomicAdd(&P.child_nkeys[parent], __popc(grp));
-      first = __shfl_sync(grp, first, leader);
-      *slot_e(L.ht, wide, slot) = first + rank;
-      uint32_t wl = __ffs(cmask) - 1;
-      uint32_t pos = 0;
-      if (lane_id() == wl) pos = atomicAdd(&L.n_new, __popc(cmask));
-      pos = __shfl_sync(cmask, pos, wl);
-      a.newslots[pos + __popc(cmask & lanemask_lt())] = slot;
-    }
     uint32_t amask = __ballot_sync(0xffffffffu, active);
+    uint32_t cw = 0, aw = 0;
+    if (lane_id() == 0) {
+      if (cmask) cw = atomicAdd(&s_cnt[0], __popc(cmask));
+      if (amask) aw = atomicAdd(&s_cnt[1], __popc(amask));
+    }
+    cw = __shfl_sync(0xffffffffu, cw, 0);
+    aw = __shfl_sync(0xffffffffu, aw, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_base[0] = s_cnt[0] ? atomicAdd(&L.n_new, s_cnt[0]) : 0u;
+      s_base[1] = s_cnt[1] ? atomicAdd(&L.n_tmp, s_cnt[1]) : 0u;
+      // Root: local key indices are the new-slot positions themselves.
+      s_base[2] = (root && s_cnt[0]) ? atomicAdd(&P.child_nkeys[0], s_cnt[0]) : 0u;
+    }
+    __syncthreads();
+    if (claimed) {
+      uint32_t cpos = cw + __popc(cmask & lanemask_lt());
+      a.newslots[s_base[0] + cpos] = slot;
+      if (root) *slot_e(L.ht, wide, slot) = s_base[2] + cpos;
+    }
+    if (!root) {
+      // Below the root: one local index per parent (grouped per warp).
+      if (claimed) {
+        uint32_t grp = __match_any_sync(cmask, parent);
+        uint32_t leader = __ffs(grp) - 1;
+        uint32_t first = 0;
+        if (lane_id() == leader) first = atomicAdd(&P.child_nkeys[parent], __popc(grp));
+        first = __shfl_sync(grp, first, leader);
+        *slot_e(L.ht, wide, slot) = first + __popc(grp & lanemask_lt());
+      }
+    }
     if (active) {
-      uint32_t grp = __match_any_sync(amask, slot);
-      if (lane_id() == __ffs(grp) - 1) atomicAdd(slot_cnt(L.ht, wide, slot), __popc(grp));
+      uint32_t o = s_base[1] + aw + __popc(amask & lanemask_lt());
+      a.tmp_row[o] = row;
+      a.tmp_slot[o] = slot;
     }
-    if (t < n) {
-      a.tmp_row[t] = row;
-      a.tmp_slot[t] = active ? slot : kNone;
-    }
+    (void)warp;
+    __syncthreads();
   }
 }
 
@@ -498,110 +566,83 @@ struct ChildFirstOp {
   __device__ void total(int job, uint32_t) const {}
 };
 
-// Pass 3: give each new slot its entry id and fill the entry arrays.
+// Pass 3: give each new slot its entry id, fill the entry arrays, and
+// allocate the entry's vector inside its parent's range (the parent's fill
+// cursor, zero at the start; one atomic per warp when the warp's entries
+// share a parent, as at the root).
 __global__ void __launch_bounds__(kThreads) k_force_assign(ForceJobs fj) {
   int2 jb = fj.jobs[blockIdx.y];
   AtomDev& a = fj.atoms[jb.x];
   LevelDev& L = a.L[jb.y];
-  const LevelDev& P = a.L[jb.y - 1];
+  LevelDev& P = a.L[jb.y - 1];
   if (L.n_req == 0) return;
   uint32_t nnew = L.n_new;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nnew; i += gridDim.x * blockDim.x) {
-    uint32_t s = a.newslots[i];
-    uint64_t kw;
-    uint32_t parent, local, cnt;
-    if (L.wide) {
-      uint4 k = L.ht[2 * size_t(s)];
-      uint4 v = L.ht[2 * size_t(s) + 1];
-      parent = k.x;
-      kw = uint64_t(parent) << 32;  // wide entries keep only the parent
-      local = v.x;
-      cnt = v.y;
-    } else {
-      uint4 sl = L.ht[s];
-      kw = s == L.mask + 1 ? kEmptyKey : ((uint64_t(sl.y) << 32) | sl.x);
-      parent = key_parent(kw, L.nk);
-      local = sl.z;
-      cnt = sl.w;
+  bool ident = jb.y == 1 && !a.root_mat;
+  uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nnew;
+       base += stride) {
+    uint32_t i = base + lane_id();
+    bool active = i < nnew;
+    uint32_t parent = 0, cnt = 0, e = 0;
+    if (active) {
+      uint32_t s = a.newslots[i];
+      uint64_t kw;
+      uint32_t local;
+      if (L.wide) {
+        uint4 k = L.ht[2 * size_t(s)];
+        uint4 v = L.ht[2 * size_t(s) + 1];
+        parent = k.x;
+        kw = uint64_t(parent) << 32;  // wide entries keep only the parent
+        local = v.x;
+        cnt = v.y;
+      } else {
+        uint4 sl = L.ht[s];
+        kw = s == L.mask + 1 ? kEmptyKey : ((uint64_t(sl.y) << 32) | sl.x);
+        parent = key_parent(kw, L.nk);
+        local = sl.z;
+        cnt = sl.w;
+      }
+      e = P.child_first[parent] + local;
+      *slot_e(L.ht, L.wide, s) = e;
+      L.key[e] = kw;
+      L.count[e] = cnt;
+      if (L.child_state) L.child_state[e] = kUnforced;
+      if (L.child_nkeys) L.child_nkeys[e] = 0;
+      if (L.child_first) L.child_first[e] = 0;
     }
-    uint32_t e = P.child_first[parent] + local;
-    *slot_e(L.ht, L.wide, s) = e;
-    L.key[e] = kw;
-    L.count[e] = cnt;
-    L.fill[e] = 0;
-    if (L.child_state) L.child_state[e] = kUnforced;
-    if (L.child_nkeys) L.child_nkeys[e] = 0;
+    uint32_t amask = __ballot_sync(0xffffffffu, active);
+    if (!amask) continue;
+    uint32_t lead = __ffs(amask) - 1;
+    uint32_t p0 = __shfl_sync(0xffffffffu, parent, lead);
+    uint32_t off;
+    if (__all_sync(0xffffffffu, !active || parent == p0)) {
+      uint32_t inc = warp_incl_scan(active ? cnt : 0u);
+      uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+      uint32_t b = 0;
+      if (lane_id() == lead) b = atomicAdd(&P.fill[p0], tot);
+      b = __shfl_sync(0xffffffffu, b, lead);
+      off = b + inc - (active ? cnt : 0u);
+    } else {
+      off = active ? atomicAdd(&P.fill[parent], cnt) : 0u;
+    }
+    if (active) {
+      uint32_t pstart = ident ? 0u : P.begin[parent];
+      L.begin[e] = pstart + off;
+      L.fill[e] = pstart + off;  // scatter cursor
+    }
   }
 }
 
-// Scan op: relative start of each new entry's vector, written into begin[]
-// (k_force_begin turns it into an absolute cursor in fill[]).
-struct EntryPosOp {
-  AtomDev* atoms;
-  const int2* jobs;
-  __device__ uint64_t n(int job) const {
-    int2 jb = jobs[job];
-    const LevelDev& L = atoms[jb.x].L[jb.y];
-    return L.n_req ? L.n_new : 0;
-  }
-  __device__ uint32_t load(int job, uint64_t i) const {
-    int2 jb = jobs[job];
-    const LevelDev& L = atoms[jb.x].L[jb.y];
-    return L.count[L.base + i];
-  }
-  __device__ void store(int job, uint64_t i, uint32_t v) const {
-    int2 jb = jobs[job];
-    const LevelDev& L = atoms[jb.x].L[jb.y];
-    L.begin[L.base + i] = v;
-  }
-  __device__ void total(int job, uint32_t v) const {
-    int2 jb = jobs[job];
-    atoms[jb.x].L[jb.y].pos_total = v;
-  }
-};
-
-// Pass 4: absolute write cursor of each new entry, inside its parent's range:
-// fill[e] = parent begin + (relative start of e - relative start of the
-// parent's first child).  Reads begin[], writes fill[] only.
-__global__ void __launch_bounds__(kThreads) k_force_begin(ForceJobs fj) {
-  int2 jb = fj.jobs[blockIdx.y];
-  AtomDev& a = fj.atoms[jb.x];
-  LevelDev& L = a.L[jb.y];
-  const LevelDev& P = a.L[jb.y - 1];
-  if (L.n_req == 0) return;
-  uint32_t nnew = L.n_new;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nnew; i += gridDim.x * blockDim.x) {
-    uint32_t e = L.base + i;
-    uint32_t parent = L.wide ? uint32_t(L.key[e] >> 32) : key_parent(L.key[e], L.nk);
-    uint32_t first = P.child_first[parent];
-    uint32_t pstart = (jb.y == 1 && !a.root_mat) ? 0u : P.begin[parent];
-    L.fill[e] = pstart + (L.begin[e] - L.begin[first]);
-  }
-}
-
-// Pass 5: move every row to its entry's range (fill[] is the cursor).
+// Pass 5: move every staged row to its entry's range (fill[] is the cursor).
 __global__ void __launch_bounds__(kThreads) k_force_scatter(ForceJobs fj) {
   int2 jb = fj.jobs[blockIdx.y];
   AtomDev& a = fj.atoms[jb.x];
   LevelDev& L = a.L[jb.y];
   if (L.n_req == 0) return;
-  uint32_t n = L.n_rows;
-  uint32_t stride = gridDim.x * blockDim.x;
-  uint32_t start = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-  for (uint32_t base = start; base < n; base += stride) {
-    uint32_t t = base + lane_id();
-    uint32_t slot = t < n ? a.tmp_slot[t] : kNone;
-    bool active = slot != kNone;
-    uint32_t e = active ? *slot_e(L.ht, L.wide, slot) : 0;
-    uint32_t amask = __ballot_sync(0xffffffffu, active);
-    if (active) {
-      uint32_t grp = __match_any_sync(amask, e);
-      uint32_t leader = __ffs(grp) - 1;
-      uint32_t first = 0;
-      if (lane_id() == leader) first = atomicAdd(&L.fill[e], __popc(grp));
-      first = __shfl_sync(grp, first, leader);
-      a.perm[first + __popc(grp & lanemask_lt())] = a.tmp_row[t];
-    }
+  uint32_t n = L.n_tmp;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    uint32_t e = *slot_e(L.ht, L.wide, a.tmp_slot[t]);
+    a.perm[atomicAdd(&L.fill[e], 1u)] = a.tmp_row[t];
   }
 }
 
@@ -617,24 +658,21 @@ __global__ void __launch_bounds__(kThreads) k_force_finish(ForceJobs fj, ResultD
   if (nreq == 0) return;
   uint32_t nnew = L.n_new;
   uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  for (uint32_t i = tid; i < nnew; i += stride) {
-    uint32_t e = L.base + i;
-    L.begin[e] = L.fill[e] - L.count[e];
-  }
+  for (uint32_t i = tid; i < nnew; i += stride) L.fill[L.base + i] = 0;  // child cursor
   for (uint32_t i = tid; i < nreq; i += stride) P.child_state[L.req[i]] = kForced;
   if (tid == 0) {
     if (jb.y == 1) {
-      a.n_pass = L.pos_total;
+      a.n_pass = L.n_tmp;
       a.root_mat = 1;
       P.begin[0] = 0;
-      P.count[0] = L.pos_total;
+      P.count[0] = L.n_tmp;
       atomicAdd(&res->ctr[FJ_CTR_ROOTS_BUILT], 1ull);
       atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
                1ull << jb.x);
     } else {
       atomicAdd(&res->ctr[FJ_CTR_SUBTRIES_FORCED], (unsigned long long)nreq);
     }
-    atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)L.pos_total);
+    atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)L.n_tmp);
     L.n_entries = L.base + nnew;
     L.cleared = 1;
   }

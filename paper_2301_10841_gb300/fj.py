@@ -30,8 +30,10 @@ COVER = {"static": 0, "fewest": 1, "learned": 2}
 OUT = {"materialize": 0, "count": 1, "count_min": 2}
 FLAG_EAGER_ALL = 1
 FLAG_EAGER_ROOT = 2
+FLAG_TIMING = 4
 CTR = {"cover_iters": 0, "probes": 1, "probe_hits": 2, "roots_built": 3, "subtries_forced": 4,
-       "rows_regrouped": 5, "survivors": 6, "chunks": 7, "kernels": 8, "atom_built_mask": 9}
+       "rows_regrouped": 5, "survivors": 6, "chunks": 7, "kernels": 8, "atom_built_mask": 9,
+       "expand_ns": 10, "expand_launches": 11, "build_ns": 12, "span_ns": 13}
 
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "INVALID_PLAN", -3: "OOM", -4: "OUTPUT_OVERFLOW",
           -5: "COUNT_OVERFLOW", -6: "TIMEOUT", -7: "CUDA", -8: "UNSUPPORTED"}
@@ -112,6 +114,8 @@ _sig = {
     "fj_build_colt_level": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "fj_execute_prepared": ([_vp, _P(_Result)], ctypes.c_int),
     "fj_reset_prepared": ([_vp], ctypes.c_int),
+    "fj_execute_prepared_async": ([_vp], ctypes.c_int),
+    "fj_prepared_result": ([_vp, _P(_Result)], ctypes.c_int),
     "fj_prepared_free": ([_vp], None),
     "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
     "fj_result_free": ([_vp, _P(_Result)], None),
@@ -377,6 +381,16 @@ class Prepared:
     def execute(self):
         res = _Result()
         _check(_lib.fj_execute_prepared(self.handle, ctypes.byref(res)))
+        tuples = _take_tuples(self.ctx, res, res.n_head) if self.out_mode == "materialize" else None
+        return Result(res, tuples, self.min_vars)
+
+    def execute_async(self):
+        """Enqueue an execution; :meth:`result` waits for it."""
+        _check(_lib.fj_execute_prepared_async(self.handle))
+
+    def result(self):
+        res = _Result()
+        _check(_lib.fj_prepared_result(self.handle, ctypes.byref(res)))
         tuples = _take_tuples(self.ctx, res, res.n_head) if self.out_mode == "materialize" else None
         return Result(res, tuples, self.min_vars)
 
