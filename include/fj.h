@@ -68,8 +68,8 @@ typedef struct fj_prepared fj_prepared;
  * FJ_ERR_CUDA. */
 fj_status fj_ctx_create(int device, void* cuda_stream, fj_ctx** out);
 
-/* Release every relation, prepared plan and buffer the context owns.  Safe on
- * NULL. */
+/* Release every relation, prepared plan and buffer the context owns (their
+ * handles become invalid: do not release them again).  Safe on NULL. */
 void fj_ctx_destroy(fj_ctx* ctx);
 
 /* Replace the stream work is enqueued on (same device).  FJ_ERR_INVALID_ARG

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -44,6 +45,8 @@ struct fj_ctx {
   ResultDev* h_res = nullptr;   // pinned
   uint64_t* h_total = nullptr;  // pinned
   void* d_partials = nullptr;   // scan partials: kMaxScanJobs x kScanBlocks x 8 B
+  std::set<fj_prepared*> preps;  // live prepared plans (released by destroy)
+  std::set<fj_rel*> rels;        // live relations (released by destroy)
 };
 
 namespace {
@@ -161,12 +164,9 @@ struct fj_prepared {
   size_t smem_expand = 0;
   int expand_blocks_per_sm = 1;
   int expand_r = 8;
-  // Node 0 streamed from its cover's base table (k_scan_probe).
+  // Node 0 streamed from its cover's base table (the scan pipeline).
   bool scan0 = false;
   ScanDev sc0{};
-  int scan_r = 8;
-  size_t scan_smem = 0;
-  int scan_blocks_per_sm = 1;
   uint64_t kernels = 0;
   uint64_t chunks = 0;
   bool explicit_built = false;  // levels built outside the join since reset
@@ -276,19 +276,26 @@ void expand_setup(int r, size_t smem, int* blocks) {
   }
 }
 
-constexpr int kScanR = 8;  // rows per lane per warp tile of the scan kernel
+constexpr int kScanR = 4;  // rows per thread per block iteration of k_scan_first
 
-void scan_attrs(size_t smem, int* blocks) {
-  const void* fn = reinterpret_cast<const void*>(&k_scan_probe<kScanR>);
-  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, smem));
-  if (*blocks < 1) *blocks = 1;
-}
-
-void launch_scan(fj_prepared* P, int grid, const NodeDev& nd) {
+// Node 0 through the scan pipeline for positions [c0, c1) of its cover.
+void run_scan_chunk(fj_prepared* P, NodeDev& nd) {
   fj_ctx* c = P->ctx;
-  k_scan_probe<kScanR><<<grid, kThreads, P->scan_smem, c->stream>>>(nd, P->sc0, P->d_atoms,
-                                                                    c->d_res);
+  cudaStream_t s = c->stream;
+  const ScanDev& sc = P->sc0;
+  int cap_blocks = c->n_sm * 8;
+  k_scan_reset<<<1, 32, 0, s>>>(sc);
+  int g1 = blocks_for(nd.chunk_end - nd.chunk_begin, kScanR * kThreads, cap_blocks);
+  k_scan_first<kScanR><<<g1, kThreads, 0, s>>>(nd, sc, c->d_res);
+  CK_LAUNCH("scan first");
+  P->kernels += 2;
+  // Survivors are about a tenth of the rows in a selective join; size the
+  // grid for a quarter of them, the loop strides over the rest.
+  uint64_t est = std::max<uint64_t>(1, (nd.chunk_end - nd.chunk_begin) / 4);
+  int g2 = blocks_for(est, 4 * kThreads, cap_blocks);
+  k_scan_rest<4><<<g2, kThreads, 0, s>>>(nd, sc, P->d_atoms, c->d_res);
+  CK_LAUNCH("scan rest");
+  P->kernels += 1;
 }
 
 void launch_expand(fj_prepared* P, int grid, const NodeDev& nd) {
@@ -339,21 +346,21 @@ void run_node(fj_prepared* P, int k, uint64_t ub_items) {
   if (total == 0) return;
   bool items_mode = nd.mode == kModeItems;
   uint64_t step = items_mode ? P->items[k + 1].cap : total;
+  if (use_scan) step = std::min<uint64_t>(step, P->sc0.cap);
   for (uint64_t c0 = 0; c0 < total; c0 += step) {
     nd.chunk_begin = c0;
     nd.chunk_end = std::min(total, c0 + step);
     if (items_mode) CK(cudaMemsetAsync(P->items[k + 1].n, 0, sizeof(uint32_t), s));
     cudaEvent_t t0 = P->timing() ? P->mark() : nullptr;
     if (use_scan) {
-      int grid = blocks_for(nd.chunk_end - c0, P->scan_r * kThreads, c->n_sm * P->scan_blocks_per_sm);
-      launch_scan(P, grid, nd);
+      run_scan_chunk(P, nd);
     } else {
       int grid = blocks_for(nd.chunk_end - c0, nd.tile, c->n_sm * P->expand_blocks_per_sm);
       launch_expand(P, grid, nd);
+      CK_LAUNCH("expand");
+      P->kernels += 1;
     }
-    CK_LAUNCH("expand");
     if (t0) P->t_expand.emplace_back(t0, P->mark());
-    P->kernels += 1;
     P->chunks += 1;
     if (items_mode) run_node(P, k + 1, nd.chunk_end - c0);
   }
@@ -776,7 +783,8 @@ static void finalize_nodes(fj_prepared* P) {
 }
 
 // Node 0 iterates its cover's base table: resolve every probe's key columns
-// (all from the cover row) and the cover's predicates for k_scan_probe.
+// (all from the cover row) and the cover's predicates for the scan
+// pipeline, and allocate its two survivor buffers.
 static void setup_scan(fj_prepared* P) {
   P->scan0 = false;
   NodeDev& N = P->nd[0];
@@ -785,6 +793,7 @@ static void setup_scan(fj_prepared* P) {
   const AtomDev& ca = P->host_atoms[C.atom];
   ScanDev sc{};
   sc.n_probe = N.n_probe;
+  bool track = false;
   for (int p = 0; p < N.n_probe; ++p) {
     const ProbeDev& Pd = N.probe[p];
     ScanProbe& S = sc.probe[p];
@@ -802,10 +811,11 @@ static void setup_scan(fj_prepared* P) {
     S.filter = Pd.filter;
     S.filter_words = Pd.filter_words;
     S.filter_on = Pd.filter_on;
+    track |= Pd.last;
   }
   if (sc.n_probe > 0) {
     const ScanProbe& F = sc.probe[0];
-    sc.k1 = F.nk == 1 && !F.wide && !F.last;
+    sc.k1 = F.nk == 1 && !F.wide;
     sc.vec_ok = sc.k1 && !(reinterpret_cast<uintptr_t>(F.kcol[0]) & 15);
   }
   sc.n_preds = ca.n_preds;
@@ -814,10 +824,19 @@ static void setup_scan(fj_prepared* P) {
     sc.pred_op[p] = ca.pred_op[p];
     sc.pred_val[p] = ca.pred_val[p];
   }
-  for (int p = 0; p < sc.n_probe; ++p) sc.track |= sc.probe[p].last;
-  P->scan_r = kScanR;
-  P->scan_smem = size_t(kThreads / 32) * scan_queue_bytes(N.n_probe, sc.track);
-  scan_attrs(P->scan_smem, &P->scan_blocks_per_sm);
+  // Survivor buffers, sized for one chunk of cover rows (a multiple of 4096
+  // rows, so chunks keep 16-byte alignment).
+  uint64_t rows = std::max<uint64_t>(ca.n_rows, 1);
+  uint32_t cap = uint32_t(std::min<uint64_t>((rows + 4095) & ~4095ull, 1ull << 24));
+  sc.cap = cap;
+  for (int b = 0; b < 1; ++b) {
+    ScanBuf& B = sc.buf[b];
+    B.row = P->alloc<uint32_t>(cap);
+    for (int p = 0; p < sc.n_probe; ++p)
+      if (!sc.probe[p].last) B.h[p] = P->alloc<uint32_t>(cap);
+    B.mult = track ? P->alloc<uint64_t>(cap) : nullptr;
+    B.n = P->alloc<uint32_t>(1);
+  }
   P->sc0 = sc;
   P->scan0 = true;
 }
@@ -971,6 +990,7 @@ static void prepared_result(fj_prepared* P, fj_result* out) {
 
 static void prepared_release(fj_prepared* P) {
   if (!P) return;
+  P->ctx->preps.erase(P);
   for (cudaEvent_t e : P->events) cudaEventDestroy(e);
   for (void* p : P->allocs) dfree(P->ctx, p);
   if (P->d_out) dfree(P->ctx, P->d_out);
@@ -1020,6 +1040,7 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
     for (void* p : P->allocs) dfree(ctx, p);
     throw;
   }
+  ctx->preps.insert(P.get());
   return P.release();
 }
 
@@ -1060,6 +1081,8 @@ fj_status fj_ctx_create(int device, void* cuda_stream, fj_ctx** out) {
 void fj_ctx_destroy(fj_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  while (!c->preps.empty()) prepared_release(*c->preps.begin());
+  while (!c->rels.empty()) fj_release_relation(c, *c->rels.begin());
   dfree(c, c->d_res);
   dfree(c, c->d_partials);
   cudaStreamSynchronize(c->stream);
@@ -1093,6 +1116,7 @@ fj_status fj_load_relation(fj_ctx* c, const char* name, int n_cols, const int32_
       }
       r->cols.push_back(d_cols[j]);
     }
+    c->rels.insert(r);
     *out = r;
   });
 }
@@ -1121,13 +1145,16 @@ fj_status fj_load_relation_host(fj_ctx* c, const char* name, int n_cols,
       for (void* p : r->owned) dfree(c, p);
       throw;
     }
+    c->rels.insert(r.get());
     *out = r.release();
   });
 }
 
 void fj_release_relation(fj_ctx* c, fj_rel* r) {
   if (!r) return;
-  for (void* p : r->owned) dfree(c ? c : r->ctx, p);
+  fj_ctx* owner = r->ctx;
+  for (void* p : r->owned) dfree(owner, p);
+  owner->rels.erase(r);
   delete r;
 }
 

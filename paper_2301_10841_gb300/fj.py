@@ -263,6 +263,7 @@ class Context:
             stream = _current_stream()
         _check(_lib.fj_ctx_create(int(device), _vp(stream), ctypes.byref(self.handle)))
         self.device = device
+        self._children = []  # weak references to relations and prepared plans
 
     def set_stream(self, stream):
         _check(_lib.fj_ctx_set_stream(self.handle, _vp(stream)))
@@ -275,8 +276,18 @@ class Context:
         """Copy host columns (numpy int32 arrays or CPU tensors) to the device."""
         return Relation(self, cols, name, host=True)
 
+    def _adopt(self, obj):
+        import weakref
+        self._children.append(weakref.ref(obj))
+
     def close(self):
         if self.handle:
+            # fj_ctx_destroy releases every relation and prepared plan.
+            for ref in self._children:
+                obj = ref()
+                if obj is not None:
+                    obj.handle = _vp()
+            self._children = []
             _lib.fj_ctx_destroy(self.handle)
             self.handle = _vp()
 
@@ -313,11 +324,12 @@ class Relation:
         fn = _lib.fj_load_relation_host if host else _lib.fj_load_relation
         _check(fn(ctx.handle, name.encode(), len(ptrs), arr, int(n or 0), ctypes.byref(self.handle)))
         self.n_rows = int(n or 0)
+        ctx._adopt(self)
 
     def release(self):
-        if self.handle:
+        if self.handle and self.ctx.handle:
             _lib.fj_release_relation(self.ctx.handle, self.handle)
-            self.handle = _vp()
+        self.handle = _vp()
 
 
 class Result:
@@ -374,6 +386,7 @@ class Prepared:
         o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags)
         self.handle = _vp()
         _check(_lib.fj_prepare(ctx.handle, q.ptr, p.ptr, ctypes.byref(o), ctypes.byref(self.handle)))
+        ctx._adopt(self)
 
     def build_level(self, atom, level):
         _check(_lib.fj_build_colt_level(self.handle, int(atom), int(level)))
@@ -398,9 +411,9 @@ class Prepared:
         _check(_lib.fj_reset_prepared(self.handle))
 
     def free(self):
-        if self.handle:
+        if self.handle and self.ctx.handle:
             _lib.fj_prepared_free(self.handle)
-            self.handle = _vp()
+        self.handle = _vp()
 
     def __del__(self):
         try:

@@ -237,3 +237,20 @@ def test_errors_are_reported(fj, ctx):
         fj.execute(ctx, dev, fj.binary_to_free_plan(dev, [0, 1]), out_mode="count_min",
                    min_vars=[9])
     assert ei.value.status == -1
+
+
+def test_context_close_releases_live_children(fj):
+    """fj_ctx_destroy releases relations and prepared plans still alive; the
+    binding's handles become inert, so later frees are no-ops."""
+    import gc
+    c = fj.Context(0)
+    e = G.uniform_digraph(50, 300, seed=9)
+    atoms, _ = device_atoms(fj, c, G.triangle_query(e))
+    plan = [[(0, (0, 1)), (1, (1,)), (2, (0,))], [(1, (2,)), (2, (2,))]]
+    p = fj.Prepared(c, atoms, plan, out_mode="count")
+    want = p.execute().count
+    c.close()
+    p.free()
+    del p, atoms
+    gc.collect()
+    assert want == oracle.binary_join(G.triangle_query(e))[0]
