@@ -6,8 +6,8 @@
  * Traditional Joins" (arXiv 2301.10841).  The library takes what the paper's
  * entry point takes (Section 5.1): base relations stored column-wise and a
  * full conjunctive query (Section 2.1, Eq. 1), plus either a left-deep binary
- * plan to convert (Section 4.1) or a Free Join plan (Def. 3.3).  It builds
- * COLT levels lazily on the GPU (Section 4.2, Def. 4.1) and runs the plan
+ * plan to convert (Section 4.1) or a Free Join plan (Def. 3.5).  It builds
+ * COLT levels lazily on the GPU (Section 4.2, Def. 4.2) and runs the plan
  * with vectorized, batch-at-a-time execution (Section 4.3) and the
  * fewest-keys dynamic cover (Section 4.4).
  *
@@ -36,7 +36,7 @@ typedef int32_t fj_status;
 
 #define FJ_OK 0
 #define FJ_ERR_INVALID_ARG (-1)      /* bad pointer, size or id */
-#define FJ_ERR_INVALID_PLAN (-2)     /* violates Def. 3.3 / Def. 3.4 */
+#define FJ_ERR_INVALID_PLAN (-2)     /* violates Def. 3.5 / Def. 3.7 */
 #define FJ_ERR_OOM (-3)              /* device allocation failed */
 #define FJ_ERR_OUTPUT_OVERFLOW (-4)  /* materialized output above list_limit */
 #define FJ_ERR_COUNT_OVERFLOW (-5)   /* COUNT(*) does not fit in uint64 */
@@ -111,7 +111,7 @@ void fj_release_relation(fj_ctx* ctx, fj_rel* rel);
 uint64_t fj_relation_rows(const fj_rel* rel);
 
 /* ------------------------------------------------------------------------ */
-/* Queries and plans (Section 2.1 Eq. 1; Section 3.2 Def. 3.2-3.4)           */
+/* Queries and plans (Section 2.1 Eq. 1; Section 3.2 Def. 3.4-3.7)           */
 /* ------------------------------------------------------------------------ */
 
 /* Pushed-down selection on one atom column (Section 2.1: "selections are
@@ -151,7 +151,7 @@ typedef struct {
   const int* head_vars;
 } fj_query;
 
-/* A subatom R(y) with y a subset of the atom's variables (Def. 3.2).  The
+/* A subatom R(y) with y a subset of the atom's variables (Def. 3.4).  The
  * variables may be listed in any order; the library uses the atom's column
  * order.  n_vars may be 0 (the empty subatom R(), which iterates the leaf
  * vector, i.e. the multiplicity). */
@@ -167,7 +167,7 @@ typedef struct {
   const fj_subatom* sub;
 } fj_node;
 
-/* A Free Join plan [phi_0 .. phi_{n-1}] (Def. 3.3).  When returned by the
+/* A Free Join plan [phi_0 .. phi_{n-1}] (Def. 3.5).  When returned by the
  * library, every array it points to is owned by the plan and released by
  * fj_plan_free. */
 typedef struct {
@@ -176,17 +176,17 @@ typedef struct {
 } fj_plan;
 
 /* Check that `plan` partitions every atom of `query` into subatoms
- * (Def. 3.3) and is valid (Def. 3.4: no two subatoms of one atom in a node;
+ * (Def. 3.5) and is valid (Def. 3.7: no two subatoms of one atom in a node;
  * every node has a cover, i.e. a subatom holding vs(phi_k) - avs(phi_k)),
  * and that sub[0] of every node is a cover.  Host only.  Returns FJ_OK or
  * FJ_ERR_INVALID_PLAN / FJ_ERR_INVALID_ARG with the reason in
  * fj_last_error(). */
 fj_status fj_validate_plan(const fj_query* query, const fj_plan* plan);
 
-/* binary2fj (Section 4.1, Fig. 12): convert the left-deep binary plan
+/* binary2fj (Section 4.1, Fig. 9): convert the left-deep binary plan
  * [R_order[0], ..., R_order[n-1]] (atom indices, a permutation of
  * 0..n_atoms-1) into a Free Join plan; then, if apply_factor != 0, apply
- * factor (Fig. 13), moving probe subatoms one node earlier while their
+ * factor (Fig. 10), moving probe subatoms one node earlier while their
  * variables are available there and the earlier node has no subatom of the
  * same atom, stopping at the first that cannot move.  Host only.  *out is
  * library-owned; release with fj_plan_free.  Errors: FJ_ERR_INVALID_ARG. */
@@ -205,14 +205,14 @@ void fj_plan_free(fj_plan* plan);
 fj_status fj_ght_schema(const fj_query* query, const fj_plan* plan, int atom,
                         int* n_levels, int* level_sizes, int* vars_out);
 
-/* Covers of node k (Def. 3.4): writes the indices into node.sub of every
+/* Covers of node k (Def. 3.7): writes the indices into node.sub of every
  * subatom that holds vs(phi_k) - avs(phi_k); *n_covers receives how many
  * (capacity FJ_MAX_SUB).  Host only. */
 fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
                          int* n_covers, int* covers_out);
 
 /* ------------------------------------------------------------------------ */
-/* Execution (Section 3.3 Fig. 7; Section 4.2 COLT; Section 4.3 Fig. 11;      */
+/* Execution (Section 3.3 Fig. 7; Section 4.2 COLT; Section 4.3 Fig. 13;      */
 /* Section 4.4 dynamic cover)                                                */
 /* ------------------------------------------------------------------------ */
 
@@ -234,7 +234,7 @@ fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
                                   device times in the FJ_CTR_*_NS counters */
 
 typedef struct {
-  uint32_t batch_size;   /* cover tuples per vectorized batch (Fig. 11);
+  uint32_t batch_size;   /* cover tuples per vectorized batch (Fig. 13);
                             0 = default 2048; rounded to a supported size */
   float load_factor;     /* COLT hash-level occupancy target; 0 = 0.5 */
   int cover_policy;      /* FJ_COVER_* */

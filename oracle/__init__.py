@@ -12,8 +12,8 @@ Contents (each function cites the paper passage it follows):
                            (Section 2.3, Fig. 2b), C++ in ``fj_oracle.cpp``.
 * :func:`brute_force`   -- nested loop over every combination of rows, the
                            plain definition of the bag join (Section 2.1, Eq. 1).
-* :mod:`oracle.plan`    -- ``binary2fj`` (Fig. 12), ``factor`` (Fig. 13),
-                           plan validity and covers (Def. 3.3-3.4) and GHT
+* :mod:`oracle.plan`    -- ``binary2fj`` (Fig. 9), ``factor`` (Fig. 10),
+                           plan validity and covers (Def. 3.5-3.7) and GHT
                            schemas (Section 3.3), in plain Python.
 * :mod:`oracle.closed`  -- closed forms and library routines used as pins
                            (trace of adjacency powers, complete-graph counts,

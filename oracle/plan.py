@@ -2,18 +2,18 @@
 
 A plan is a list of nodes; a node is a list of subatoms; a subatom is a pair
 ``(atom_index, tuple_of_vars)``.  The first subatom of a node is its
-designated cover (Section 3.2, the convention after Def. 3.4).  Atoms are the
+designated cover (Section 3.2, the convention after Def. 3.7).  Atoms are the
 query's atoms, given as their variable lists (``atom_vars[i]``).
 
 Readings of passages the paper leaves open (each also listed in the design doc):
 
-* ``binary2fj`` (Fig. 12): the "available variables" used while building the
+* ``binary2fj`` (Fig. 9): the "available variables" used while building the
   current node are all variables bound so far, including those of the
   current node -- otherwise the chain example of Section 4.1 would not come
   out as printed.  A relation whose variables are already all bound gets an
   empty subatom ``s()`` as its own node; it stands for the leaf vector, whose
   length is the bag multiplicity.
-* ``factor`` (Fig. 13): only the non-cover subatoms of a node are candidates
+* ``factor`` (Fig. 10): only the non-cover subatoms of a node are candidates
   to move, visited in order, and the first one that cannot move stops the
   node (the conservative rule).  Otherwise the clover plan printed in
   Section 4.1 would not come out as printed.  Nodes are visited from the last
@@ -30,7 +30,7 @@ def _ordered(atom_vars, a, subset):
 
 
 def vs(node):
-    """vs(phi): all variables of all subatoms of a node (Def. 3.3)."""
+    """vs(phi): all variables of all subatoms of a node (Def. 3.5)."""
     out = set()
     for _, vars_ in node:
         out |= set(vars_)
@@ -38,7 +38,7 @@ def vs(node):
 
 
 def avs(plan, k):
-    """avs(phi_k): union of vs(phi_j) for j < k (Def. 3.3)."""
+    """avs(phi_k): union of vs(phi_j) for j < k (Def. 3.5)."""
     out = set()
     for j in range(k):
         out |= vs(plan[j])
@@ -46,7 +46,7 @@ def avs(plan, k):
 
 
 def binary2fj(atom_vars, order):
-    """Left-deep binary plan ``order`` -> Free Join plan (Section 4.1, Fig. 12)."""
+    """Left-deep binary plan ``order`` -> Free Join plan (Section 4.1, Fig. 9)."""
     r = order[0]
     phi = [(r, tuple(atom_vars[r]))]
     bound = set(atom_vars[r])
@@ -61,7 +61,7 @@ def binary2fj(atom_vars, order):
 
 
 def factor(plan):
-    """Move probes one node earlier, conservatively (Section 4.1, Fig. 13)."""
+    """Move probes one node earlier, conservatively (Section 4.1, Fig. 10)."""
     plan = [list(node) for node in plan]
     n = len(plan)
     for i in range(n - 1, 0, -1):
@@ -78,13 +78,13 @@ def factor(plan):
 
 
 def covers(plan, k):
-    """Subatoms of node k containing vs(phi_k) - avs(phi_k) (Def. 3.4)."""
+    """Subatoms of node k containing vs(phi_k) - avs(phi_k) (Def. 3.7)."""
     need = vs(plan[k]) - avs(plan, k)
     return [i for i, (_, vars_) in enumerate(plan[k]) if need <= set(vars_)]
 
 
 def is_valid(atom_vars, plan):
-    """Partition requirement (Def. 3.3) and validity (Def. 3.4)."""
+    """Partition requirement (Def. 3.5) and validity (Def. 3.7)."""
     seen = {a: [] for a in range(len(atom_vars))}
     for node in plan:
         if not node:

@@ -1,12 +1,12 @@
 // Node execution kernels: cover choice, fanout, and the vectorized expansion
-// (paper Section 3.3 Fig. 7, Section 4.3 Fig. 11, Section 4.4).
+// (paper Section 3.3 Fig. 7, Section 4.3 Fig. 13, Section 4.4).
 //
 // A node's input is a set of partial tuples ("items"): the variables bound by
 // earlier nodes, one COLT handle per atom (an entry of the atom's level that
 // earlier nodes reached), and a bag multiplicity.  Every item contributes as
 // many cover elements as its chosen cover has: the offsets of a COLT vector
 // when the cover is the atom's last level (iterated without forcing, as the
-// `is_suffix` case of Fig. 10), or the keys of a forced map otherwise.  A
+// `is_suffix` case of Fig. 12), or the keys of a forced map otherwise.  A
 // prefix sum of these fanouts maps a flat position space onto
 // (item, element), which is cut into batches of `tile` elements -- the
 // paper's batch of cover tuples -- each handled by one thread block: the
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
       }
     }
     if (tid == 0) c_iters += tn;
-    // Probe phases: one subatom at a time for the whole batch (Fig. 11).
+    // Probe phases: one subatom at a time for the whole batch (Fig. 13).
     for (int s = 0; s < nd.n_sub; ++s) {
       if (!nd.dynamic && s == 0) continue;
       const SubDev& S = nd.sub[s];

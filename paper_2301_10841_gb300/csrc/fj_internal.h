@@ -1,7 +1,7 @@
 // Internal device-side structures of libfj (shared by the host driver and the
 // kernels).  Not part of the public ABI.
 //
-// COLT layout in HBM (paper Section 4.2, Def. 4.1 and Fig. 10).  For every
+// COLT layout in HBM (paper Section 4.2, Def. 4.2 and Fig. 12).  For every
 // atom the library keeps one array of row offsets `perm` and a stack of levels
 // L[0..n_levels).  L[0] is a virtual level with a single entry standing for
 // the whole relation; L[i] (i >= 1) holds the hash-map nodes of schema level

@@ -1,12 +1,12 @@
 // Device kernels of libfj.
 //
-//  * COLT forcing (paper Section 4.2, Fig. 10 `force`): turn the child
+//  * COLT forcing (paper Section 4.2, Fig. 12 `force`): turn the child
 //    vectors of a list of parent entries into hash-map nodes of the next
 //    level, regrouping their offsets in place.  The root level is the same
 //    operation on the single virtual root entry, with the atom's pushed-down
 //    selections (Section 2.1) applied while scanning the base table.
 //  * Node expansion (Section 3.3 Fig. 7 with the batching of Section 4.3
-//    Fig. 11): iterate a batch of cover elements, probe every other subatom
+//    Fig. 13): iterate a batch of cover elements, probe every other subatom
 //    for the whole batch, drop misses, and hand the survivors to the next
 //    node, or aggregate / materialize them at the end of the plan.
 //  * Cover choice (Section 4.4): per partial tuple, the cover whose trie has

@@ -1,7 +1,7 @@
 // Free Join plans on the host: loading and checking queries and plans
-// (Section 2.1 Eq. 1; Section 3.2 Def. 3.2-3.4), converting a left-deep
-// binary plan (Section 4.1 Fig. 12, binary2fj), and factoring it (Section 4.1
-// Fig. 13, factor).
+// (Section 2.1 Eq. 1; Section 3.2 Def. 3.4-3.7), converting a left-deep
+// binary plan (Section 4.1 Fig. 9, binary2fj), and factoring it (Section 4.1
+// Fig. 10, factor).
 //
 // Readings of passages the paper leaves open:
 //  * binary2fj: the variables "available" while the current node is built
@@ -165,14 +165,14 @@ bool validate(const PQuery& q, const PPlan& plan) {
     for (const PSub& s : plan[k]) {
       if (atoms_here >> s.atom & 1) {
         set_error("invalid plan: node " + std::to_string(k) +
-                  " has two subatoms of one atom (Def. 3.4 a)");
+                  " has two subatoms of one atom (Def. 3.7 a)");
         return false;
       }
       atoms_here |= 1ull << s.atom;
       for (int v : s.vars) {
         if (got[s.atom] >> v & 1) {
           set_error("invalid plan: a variable of atom " + std::to_string(s.atom) +
-                    " appears in two subatoms (Def. 3.3)");
+                    " appears in two subatoms (Def. 3.5)");
           return false;
         }
         got[s.atom] |= 1ull << v;
@@ -181,7 +181,7 @@ bool validate(const PQuery& q, const PPlan& plan) {
     }
     auto cv = covers(plan, k);
     if (cv.empty()) {
-      set_error("invalid plan: node " + std::to_string(k) + " has no cover (Def. 3.4 b)");
+      set_error("invalid plan: node " + std::to_string(k) + " has no cover (Def. 3.7 b)");
       return false;
     }
     if (cv[0] != 0) {
@@ -195,7 +195,7 @@ bool validate(const PQuery& q, const PPlan& plan) {
     for (int v : q.atom_vars[a]) want |= 1ull << v;
     if (!appears[a] || got[a] != want) {
       set_error("invalid plan: the subatoms of atom " + std::to_string(a) +
-                " do not partition its variables (Def. 3.3)");
+                " do not partition its variables (Def. 3.5)");
       return false;
     }
   }

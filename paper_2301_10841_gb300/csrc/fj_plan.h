@@ -32,7 +32,7 @@ uint64_t vs_mask(const PNode& node);
 uint64_t avs_mask(const PPlan& plan, int k);
 std::vector<int> covers(const PPlan& plan, int k);
 
-// Def. 3.3 / Def. 3.4, plus: sub[0] of every node is a cover.
+// Def. 3.5 / Def. 3.7, plus: sub[0] of every node is a cover.
 bool validate(const PQuery& q, const PPlan& plan);
 
 PPlan binary2fj(const PQuery& q, const std::vector<int>& order);

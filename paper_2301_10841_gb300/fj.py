@@ -205,7 +205,7 @@ def _plan_from_c(pp):
 # ---------------------------------------------------------------------------
 
 def binary_to_free_plan(atoms, order=None, factor=True):
-    """binary2fj (Fig. 12) and, if ``factor``, factor (Fig. 13)."""
+    """binary2fj (Fig. 9) and, if ``factor``, factor (Fig. 10)."""
     q = _QueryC(atoms)
     order = list(range(len(atoms))) if order is None else list(order)
     out = _P(_Plan)()
@@ -218,7 +218,7 @@ def binary_to_free_plan(atoms, order=None, factor=True):
 
 
 def validate_plan(atoms, plan):
-    """Returns (True, "") or (False, reason) per Def. 3.3 / Def. 3.4."""
+    """Returns (True, "") or (False, reason) per Def. 3.5 / Def. 3.7."""
     q, p = _QueryC(atoms), _PlanC(plan)
     st = _lib.fj_validate_plan(q.ptr, p.ptr)
     return st == 0, _lib.fj_last_error().decode()

@@ -117,7 +117,7 @@ def test_star_join_reduced(fj, ctx):
 
 
 def test_clover_factor_changes_work_not_result(fj, ctx):
-    """Fig. 5 instance: one output tuple; the naive plan's second loop runs
+    """Fig. 3 instance: one output tuple; the naive plan's second loop runs
     n^2 times, the factored plan's work is linear (Section 4.1)."""
     from test_oracle import clover_instance
     n = 200
@@ -135,7 +135,7 @@ def test_clover_factor_changes_work_not_result(fj, ctx):
 
 
 def test_colt_laziness_example(fj, ctx):
-    """Example 4.2: Q(x,a,b,c) :- R(x,a),S(x,b),T(x,c),U(b) with plan
+    """Example 4.3: Q(x,a,b,c) :- R(x,a),S(x,b),T(x,c),U(b) with plan
     [[R(x,a),S(x),T(x)],[U(b),S(b)],[T(c)]] on the clover instance.  R is only
     iterated, so nothing is built for it; S and T get their first level; with
     U(b) as the cover only the x0 subtrie of S is expanded; with the fewest-

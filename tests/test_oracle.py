@@ -84,10 +84,10 @@ def test_predicates_are_applied():
             assert res[0] == want, op
 
 
-# --- the paper's worked example: the clover instance (Fig. 5) ---------------
+# --- the paper's worked example: the clover instance (Fig. 3) ---------------
 
 def clover_instance(n):
-    """Fig. 5: R = {(x0,a0)} u {(x1,a_i^l),(x2,a_i^r)}, S = {(x0,b0)} u
+    """Fig. 3: R = {(x0,a0)} u {(x1,a_i^l),(x2,a_i^r)}, S = {(x0,b0)} u
     {(x2,b_i^l),(x3,b_i^r)}, T = {(x0,c0)} u {(x3,c_i^l),(x1,c_i^r)}.
     x_j -> j; a0 -> 100, a_i^l -> 100+i, a_i^r -> 100+n+i; b and c likewise
     from 1000 and 10000 (n < 100)."""
