@@ -326,6 +326,36 @@ fj_status fj_result_copy_tuples(fj_ctx* ctx, const fj_result* res, void* dst,
 /* Release the device buffer of a result (safe to call twice). */
 void fj_result_free(fj_ctx* ctx, fj_result* res);
 
+/* ------------------------------------------------------------------------ */
+/* Join without allocation (no counterpart in the paper)                     */
+/* ------------------------------------------------------------------------ */
+
+/* The bag COUNT of the equi-join Q(x) :- R(x), S(x), computed without any
+ * device allocation, for callers that cannot allocate on this path: code
+ * running while a stream is captured into a CUDA graph, services holding a
+ * fixed pre-reserved memory budget, or hosts that provide a stream but no
+ * allocator.  The paper has no counterpart; fj_execute_plan computes the
+ * same COUNT for the same query.
+ *
+ * d_r_key (n_r values) and d_s_key (n_s values) are int32 device columns; the
+ * result is written to *d_count (a device uint64).  Work is enqueued on
+ * `cuda_stream` (a cudaStream_t, NULL for the legacy default stream) of the
+ * current device and not waited for.
+ *
+ * Scratch is a fixed 8 MiB array inside the library (held by every GPU that
+ * loads it, until the process exits), so S may have at most 524288 rows:
+ * larger inputs fail with FJ_ERR_INVALID_ARG before any GPU work.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress
+ * with the device current); make that first call before any stream capture.
+ * All calls share the array: each clears what it uses, and calls that
+ * overlap on the GPU (other streams or threads) race.  Errors:
+ * FJ_ERR_INVALID_ARG, FJ_ERR_CUDA, with the reason in
+ * fj_noalloc_last_error(). */
+fj_status fj_join2_count_noalloc(const int32_t* d_r_key, uint64_t n_r,
+                                 const int32_t* d_s_key, uint64_t n_s,
+                                 uint64_t* d_count, void* cuda_stream);
+const char* fj_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libfj.so")
-SOURCES = ["fj_engine.cu", "fj_plan.cpp"]
+SOURCES = ["fj_engine.cu", "fj_plan.cpp", "fj_noalloc.cu"]
 HEADERS = ["fj_internal.h", "fj_kernels.cuh", "fj_exec.cuh", "fj_scan.cuh", "fj_plan.h",
            os.path.join("..", "..", "include", "fj.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

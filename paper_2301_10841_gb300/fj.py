@@ -119,6 +119,9 @@ _sig = {
     "fj_prepared_free": ([_vp], None),
     "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
     "fj_result_free": ([_vp, _P(_Result)], None),
+    "fj_join2_count_noalloc": ([_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp],
+                               ctypes.c_int),
+    "fj_noalloc_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -372,6 +375,20 @@ def execute(ctx, atoms, plan, head=None, out_mode="count", min_vars=None, batch_
     finally:
         _lib.fj_result_free(ctx.handle, ctypes.byref(res))
     return Result(res, tuples, min_vars or [])
+
+
+def join2_count_noalloc(r_key, s_key, out, stream=None):
+    """Bag COUNT of R(x), S(x) into the int64 CUDA tensor `out` (one element),
+    with no device allocation (fj_join2_count_noalloc).  `r_key` and `s_key`
+    are contiguous int32 CUDA tensors; work goes on `stream` (default: the
+    current torch stream) and is not waited for."""
+    if stream is None:
+        stream = _current_stream()
+    st = _lib.fj_join2_count_noalloc(_vp(r_key.data_ptr()), r_key.numel(),
+                                     _vp(s_key.data_ptr()), s_key.numel(),
+                                     _vp(out.data_ptr()), _vp(stream))
+    if st != 0:
+        raise FJError(st, _lib.fj_noalloc_last_error().decode())
 
 
 class Prepared:
