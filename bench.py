@@ -74,7 +74,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -161,16 +161,19 @@ def measured_peaks():
 
 
 def profiled_traffic(kernel_hash):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    """DRAM bytes per launch of the dominant kernels from the committed ncu
     summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "star_expand_traffic.json")
+    import re
+    path = os.path.join(ROOT, "profiles", "scan_pipeline_star_F10M.md")
     try:
         with open(path) as f:
-            t = json.load(f)
-        if t.get("source_hash") == kernel_hash:
-            return t.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
-        pass
+            text = f.read()
+    except OSError:
+        return None
+    src = re.search(r"kernel_source:\s*([0-9a-f]+)", text)
+    tr = re.search(r"traffic_bytes_per_step:\s*([0-9]+)", text)
+    if src and tr and src.group(1) == kernel_hash:
+        return int(tr.group(1))
     return None
 
 
@@ -214,7 +217,8 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     fact, dims = G.star_schema(n_fact=N_FACT, dims=DIMS, s=1.1, seed=2)
-    n = 1_000_000
+    # A bounded prefix of F per step, so K steps stay within a few minutes.
+    n = 1_000_000 if args.steps <= 100 else max(100_000, 100_000_000 // args.steps)
     q = G.star_query({"name": "F", "cols": [c[:n] for c in fact["cols"]]}, dims, theta=THETA)
     tin = n + sum(DIMS)
     for _ in range(args.warmup):
@@ -344,7 +348,7 @@ def run_fj(args, rank, world):
     launch_s = expand_ns / max(1, expand_n) / 1e9
     achieved = alg / launch_s / 1e9 if launch_s > 0 else None
     khash = source_hash()
-    roofline = {"bound": "hbm", "kernel": "k_expand (node 0 probe phase)",
+    roofline = {"bound": "hbm", "kernel": "node-0 scan pipeline (k_scan_first + k_scan_rest)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
                 "traffic": profiled_traffic(khash), "algorithmic_bytes": alg,
@@ -366,8 +370,8 @@ def run_fj(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fj", choices=["fj", "reference"])
     ap.add_argument("--batch", type=int, default=2048)
     ap.add_argument("--n-fact", type=int, default=N_FACT)
