@@ -167,6 +167,7 @@ struct fj_prepared {
   // Node 0 streamed from its cover's base table (the scan pipeline).
   bool scan0 = false;
   ScanDev sc0{};
+  int fuse_blocks = 0;  // > 0: node 0 runs as one k_scan_fused launch of this many blocks
   uint64_t kernels = 0;
   uint64_t chunks = 0;
   bool explicit_built = false;  // levels built outside the join since reset
@@ -278,11 +279,20 @@ void expand_setup(int r, size_t smem, int* blocks) {
 
 constexpr int kScanR = 4;  // rows per thread per block iteration of k_scan_first
 
+constexpr int kFuseR = 4;  // survivors per lane per round in k_scan_fused
+
 // Node 0 through the scan pipeline for positions [c0, c1) of its cover.
 void run_scan_chunk(fj_prepared* P, NodeDev& nd) {
   fj_ctx* c = P->ctx;
   cudaStream_t s = c->stream;
   const ScanDev& sc = P->sc0;
+  if (P->fuse_blocks > 0) {
+    k_scan_fused<kFuseR><<<P->fuse_blocks, kThreads, kFuseSmem, s>>>(nd, sc, P->d_atoms,
+                                                                     c->d_res);
+    CK_LAUNCH("scan fused");
+    P->kernels += 1;
+    return;
+  }
   int cap_blocks = c->n_sm * 8;
   k_scan_reset<<<1, 32, 0, s>>>(sc);
   int g1 = blocks_for(nd.chunk_end - nd.chunk_begin, kScanR * kThreads, cap_blocks);
@@ -836,9 +846,21 @@ static void setup_scan(fj_prepared* P) {
       if (!sc.probe[p].last) B.h[p] = P->alloc<uint32_t>(cap);
     B.mult = track ? P->alloc<uint64_t>(cap) : nullptr;
     B.n = P->alloc<uint32_t>(1);
+    B.src = P->alloc<uint32_t>(cap);
   }
   P->sc0 = sc;
   P->scan0 = true;
+  // One launch per chunk when the first probe reads one 16-byte aligned key
+  // column and the cover has no selection: one resident wave of blocks.
+  P->fuse_blocks = 0;
+  if (sc.k1 && sc.vec_ok && sc.n_preds == 0) {
+    int b = 0;
+    CK(cudaFuncSetAttribute(k_scan_fused<kFuseR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            int(kFuseSmem)));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan_fused<kFuseR>, kThreads,
+                                                     kFuseSmem));
+    P->fuse_blocks = P->ctx->n_sm * std::max(1, b);
+  }
 }
 
 static void ensure_output(fj_prepared* P, uint64_t rows) {
@@ -906,6 +928,7 @@ static void read_result(fj_prepared* P, fj_result* out, bool* retry) {
   if (r.status & kStTableFull) fail(FJ_ERR_CUDA, "internal: COLT hash level overfilled");
   if (r.status & kStItemsOverflow) fail(FJ_ERR_CUDA, "internal: partial-tuple buffer overflow");
   if (r.status & kStCountOverflow) fail(FJ_ERR_COUNT_OVERFLOW, "COUNT(*) exceeds 2^64 - 1");
+  if (r.status & kStTimeout) fail(FJ_ERR_TIMEOUT, "a bounded device wait ran out");
   std::memset(out, 0, sizeof(*out));
   out->n_head = int(P->q.head.size());
   if (P->materialize) {

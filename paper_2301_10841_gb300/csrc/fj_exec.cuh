@@ -166,9 +166,8 @@ __device__ __forceinline__ uint64_t mul_sat(uint64_t a, uint64_t b, uint32_t* st
 __device__ __forceinline__ bool probe_start(const uint4* __restrict__ ht, uint32_t mask,
                                             const uint32_t* __restrict__ filt, uint32_t fwords,
                                             uint64_t kw, uint32_t& hh, uint4& sl) {
-  uint32_t h = hash_key(kw);
-  if (filt && kw != kEmptyKey && bloom_rejects(filt, fwords, h)) return false;
-  hh = h & mask;
+  if (filt && kw != kEmptyKey && bloom_rejects(filt, fwords, filter_hash(kw))) return false;
+  hh = hash_key(kw) & mask;
   sl = __ldg(&ht[hh]);
   return true;
 }

@@ -48,16 +48,30 @@ __device__ __forceinline__ uint32_t hash_key(uint64_t kw) {
   return fmix32(uint32_t(kw) ^ fmix32(uint32_t(kw >> 32) + 0x9e3779b9u));
 }
 
-// Blocked Bloom filter: word (h mod words), bits 13..17 and 18..22 of h.
-__device__ __forceinline__ uint32_t bloom_bits(uint32_t h) {
-  return (1u << ((h >> 13) & 31u)) | (1u << ((h >> 18) & 31u));
+// Blocked Bloom filter hash of a narrow key word: the high half of a
+// multiplicative (Fibonacci) hash of both halves of the word, so a key of
+// the root (parent 0) costs one wide multiply.  Independent of hash_key,
+// which places keys in the table.
+constexpr uint64_t kFibLo = 0x9e3779b97f4a7c15ull;  // 2^64 / golden ratio
+constexpr uint64_t kFibHi = 0xc2b2ae3d27d4eb4full;
+__device__ __forceinline__ uint32_t filter_hash(uint64_t kw) {
+  return uint32_t((uint64_t(uint32_t(kw)) * kFibLo + uint64_t(uint32_t(kw >> 32)) * kFibHi) >>
+                  32);
+}
+__device__ __forceinline__ uint32_t filter_hash_root1(int32_t k) {
+  return uint32_t((uint64_t(uint32_t(k)) * kFibLo) >> 32);
+}
+
+// Filter word: (fh mod words); two bits from the top ten bits of fh.
+__device__ __forceinline__ uint32_t bloom_bits(uint32_t fh) {
+  return (1u << (fh >> 27)) | (1u << ((fh >> 22) & 31u));
 }
 
 // True when the filter rules the key out (no false negatives).
 __device__ __forceinline__ bool bloom_rejects(const uint32_t* __restrict__ f, uint32_t words,
-                                              uint32_t h) {
-  uint32_t m = bloom_bits(h);
-  return (__ldg(&f[h & (words - 1)]) & m) != m;
+                                              uint32_t fh) {
+  uint32_t m = bloom_bits(fh);
+  return (__ldg(&f[fh & (words - 1)]) & m) != m;
 }
 
 // Key word of (parent, key tuple).  One level's keys all have the same arity:
@@ -494,8 +508,8 @@ __global__ void __launch_bounds__(kThreads) k_force_insert(ForceJobs fj, ResultD
         uint64_t kw = pack_key(parent, nk, nk > 0 ? c0[row] : 0, nk > 1 ? c1[row] : 0);
         slot = ht_insert(L.ht, mask, kw, claimed, &res->status);
         if (claimed && fon) {
-          uint32_t h = hash_key(kw);
-          atomicOr(&L.filter[h & (L.filter_words - 1)], bloom_bits(h));
+          uint32_t fh = filter_hash(kw);
+          atomicOr(&L.filter[fh & (L.filter_words - 1)], bloom_bits(fh));
         }
       }
       if (slot == kNone) active = false;

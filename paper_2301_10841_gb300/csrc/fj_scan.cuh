@@ -40,6 +40,7 @@ struct ScanBuf {
   uint32_t* h[FJ_MAX_SUB];  // entry reached by probe p (non-last probes)
   uint64_t* mult;           // null when no probe ends an atom at a leaf
   uint32_t* n;
+  uint32_t* src;            // k_scan_fused: position after the first probe
 };
 
 struct ScanDev {
@@ -242,10 +243,9 @@ __global__ void __launch_bounds__(kThreads) k_scan_first(const __grid_constant__
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           hv[r] = hash_root1(k[r]);
-          if (filt && (live >> r & 1u)) {
-            uint32_t m = bloom_bits(hv[r]);
-            if ((__ldg(&filt[hv[r] & (P.filter_words - 1)]) & m) != m) live &= ~(1u << r);
-          }
+          if (filt && (live >> r & 1u) &&
+              bloom_rejects(filt, P.filter_words, filter_hash_root1(k[r])))
+            live &= ~(1u << r);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -308,6 +308,198 @@ __device__ __forceinline__ uint32_t scan_handle(const ScanDev& sc, const ScanBuf
   return 0u;
 }
 
+// Remaining probes 1..n_probe-1 for R survivors of one thread, in plan
+// order; each probe's entries are kept beside the survivor (b.h[p]) for the
+// epilogue.  Returns the survivors that hit every probe.
+template <int R>
+__device__ __forceinline__ uint32_t scan_rest_probes(const ScanDev& sc, const ScanBuf& b,
+                                                     const uint32_t* s_mask,
+                                                     const uint32_t* s_fon, uint32_t live,
+                                                     const uint32_t (&idx)[R],
+                                                     const uint32_t (&row)[R], uint32_t (&e)[R],
+                                                     uint64_t (&mult)[R], uint32_t* status,
+                                                     unsigned long long& c_probe,
+                                                     unsigned long long& c_hit) {
+  for (int p = 1; p < sc.n_probe && live; ++p) {
+    const ScanProbe& P = sc.probe[p];
+    c_probe += __popc(live);
+    live = scan_probe_rows<R>(P, s_mask[p], s_fon[p] ? P.filter : nullptr, live, row, e,
+                              b.mult ? mult : nullptr, status);
+    c_hit += __popc(live);
+    if (!P.last)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (live >> r & 1u) b.h[p][idx[r]] = e[r];
+  }
+  return live;
+}
+
+// Node 0's epilogue for R survivors of one thread: partial tuples for node 1,
+// aggregation (COUNT, MIN, trailing product nodes), or output tuples.  The
+// partial tuples are appended block-wide (every thread of the block calls
+// this the same number of times) or, with WARP_APPEND, warp-wide (every lane
+// of the warp does).
+template <int R, bool WARP_APPEND = false>
+__device__ __forceinline__ void scan_epilogue(const NodeDev& nd, const ScanDev& sc,
+                                              const ScanBuf& b, AtomDev* atoms, ResultDev* res,
+                                              const uint32_t (&idx)[R], const uint32_t (&row)[R],
+                                              const uint64_t (&mult)[R], uint32_t live,
+                                              uint32_t* s_cnt, uint32_t* s_base, int32_t* s_min,
+                                              unsigned long long& my_count, bool& any) {
+  if (nd.mode == kModeItems) {
+    uint32_t pos;
+    if (WARP_APPEND) {
+      const uint32_t mine = __popc(live);
+      const uint32_t inc = warp_incl_scan(mine);
+      uint32_t b0 = 0;
+      if (lane_id() == 31 && inc) b0 = atomicAdd(nd.out_n, inc);
+      pos = __shfl_sync(0xffffffffu, b0, 31) + inc - mine;
+    } else {
+      pos = block_append(__popc(live), nd.out_n, s_cnt, s_base);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!(live >> r & 1u)) continue;
+      uint32_t o = pos++;
+      if (o >= nd.out_cap) {
+        atomicOr(&res->status, kStItemsOverflow);
+        continue;
+      }
+      for (int k = 0; k < nd.n_out_vars; ++k)
+        nd.out_var[k][o] = src_value(nd.src[nd.out_var_id[k]], 0, row[r]);
+      for (int a = 0; a < FJ_MAX_ATOMS; ++a)
+        if (nd.out_h[a]) nd.out_h[a][o] = scan_handle(sc, b, nd.out_h_src[a], idx[r]);
+      if (nd.out_mult) nd.out_mult[o] = mult[r];
+    }
+  } else if (nd.mode == kModeAggregate) {
+    constexpr int MT = 8;  // tails whose lookups are issued together
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!(live >> r & 1u)) continue;
+      uint64_t m = mult[r];
+      const int nt = nd.n_tail;
+      uint32_t th[MT], cn[MT], pr[MT];
+      if (nt <= MT) {
+        // Each tail's vector: handle, then length and first offset, then
+        // the first row, every level of lookups in flight for all tails.
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+          th[t] = t < nt ? scan_handle(sc, b, nd.tail[t].hsrc, idx[r]) : 0u;
+        uint32_t bg[MT];
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+          cn[t] = 1;
+          bg[t] = 0;
+          if (t < nt) {
+            const LevelDev& L = atoms[nd.tail[t].atom].L[nd.tail[t].lvl];
+            cn[t] = L.count[th[t]];
+            if (nd.tail[t].n_min) bg[t] = L.begin[th[t]];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+          pr[t] = 0;
+          if (t < nt && nd.tail[t].n_min && cn[t]) pr[t] = atoms[nd.tail[t].atom].perm[bg[t]];
+          if (t < nt) m = mul_sat(m, cn[t], &res->status);
+        }
+        if (!m) continue;
+        unsigned long long before = my_count;
+        my_count += m;
+        if (my_count < before) atomicOr(&res->status, kStCountOverflow);
+        any = true;
+        for (int k = 0; k < nd.n_min; ++k)
+          atomicMin(&s_min[nd.min_idx[k]], src_value(nd.src[nd.min_var[k]], 0, row[r]));
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+          if (t >= nt || !nd.tail[t].n_min) continue;
+          const TailDev& td = nd.tail[t];
+          const AtomDev& ta = atoms[td.atom];
+          for (int k = 0; k < td.n_min; ++k) {
+            const int32_t* col = ta.cols[td.min_col[k]];
+            int32_t lo = col[pr[t]];
+            for (uint32_t x = 1; x < cn[t]; ++x) lo = min(lo, col[ta.perm[bg[t] + x]]);
+            atomicMin(&s_min[td.min_idx[k]], lo);
+          }
+        }
+        continue;
+      }
+      for (int t = 0; t < nd.n_tail && m; ++t) {
+        const TailDev& td = nd.tail[t];
+        const AtomDev& ta = atoms[td.atom];
+        m = mul_sat(m, ta.L[td.lvl].count[scan_handle(sc, b, td.hsrc, idx[r])], &res->status);
+      }
+      if (!m) continue;
+      unsigned long long before = my_count;
+      my_count += m;
+      if (my_count < before) atomicOr(&res->status, kStCountOverflow);
+      any = true;
+      for (int k = 0; k < nd.n_min; ++k)
+        atomicMin(&s_min[nd.min_idx[k]], src_value(nd.src[nd.min_var[k]], 0, row[r]));
+      for (int t = 0; t < nd.n_tail; ++t) {
+        const TailDev& td = nd.tail[t];
+        if (!td.n_min) continue;
+        const AtomDev& ta = atoms[td.atom];
+        uint32_t h = scan_handle(sc, b, td.hsrc, idx[r]);
+        uint32_t bg = ta.L[td.lvl].begin[h], cn = ta.L[td.lvl].count[h];
+        for (int k = 0; k < td.n_min; ++k) {
+          const int32_t* col = ta.cols[td.min_col[k]];
+          int32_t lo = INT32_MAX;
+          for (uint32_t x = 0; x < cn; ++x) lo = min(lo, col[ta.perm[bg + x]]);
+          atomicMin(&s_min[td.min_idx[k]], lo);
+        }
+      }
+    }
+  } else {  // kModeMaterialize
+    uint64_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (live >> r & 1u) tot += mult[r];
+    uint64_t inc = warp_incl_scan<unsigned long long>(tot);
+    uint64_t base = 0;
+    if (lane_id() == 31 && inc) base = atomicAdd(&res->n_out, (unsigned long long)inc);
+    base = __shfl_sync(0xffffffffu, (unsigned long long)base, 31) + inc - tot;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!(live >> r & 1u)) continue;
+      for (uint64_t x = 0; x < mult[r]; ++x) {
+        uint64_t orow = base++;
+        if (orow >= nd.out_rows_cap) {
+          atomicOr(&res->status, kStOutputOverflow);
+          continue;
+        }
+        for (int h = 0; h < nd.n_head; ++h)
+          nd.out_tuples[orow * nd.n_head + h] = src_value(nd.src[nd.head_var[h]], 0, row[r]);
+      }
+    }
+  }
+}
+
+// Block totals of node 0 into the result: COUNT and MIN (aggregate mode)
+// and the probe counters.
+__device__ __forceinline__ void scan_block_totals(const NodeDev& nd, ResultDev* res,
+                                                  int32_t* s_min, unsigned long long* s_red,
+                                                  unsigned long long my_count, bool any,
+                                                  unsigned long long surv,
+                                                  unsigned long long c_probe,
+                                                  unsigned long long c_hit) {
+  if (nd.mode == kModeAggregate) {
+    unsigned long long tot = block_sum<unsigned long long>(my_count, s_red);
+    int any_b = __syncthreads_or(any);
+    if (threadIdx.x == 0 && tot) {
+      unsigned long long old = atomicAdd(&res->count, tot);
+      if (old + tot < old) atomicOr(&res->status, kStCountOverflow);
+    }
+    if (any_b && threadIdx.x < FJ_MAX_VARS)
+      atomicMin(&res->mins[threadIdx.x], s_min[threadIdx.x]);
+  }
+  unsigned long long v = block_sum<unsigned long long>(surv, s_red);
+  if (threadIdx.x == 0 && v) atomicAdd(&res->ctr[FJ_CTR_SURVIVORS], v);
+  v = block_sum<unsigned long long>(c_probe, s_red);
+  if (threadIdx.x == 0 && v) atomicAdd(&res->ctr[FJ_CTR_PROBES], v);
+  v = block_sum<unsigned long long>(c_hit, s_red);
+  if (threadIdx.x == 0 && v) atomicAdd(&res->ctr[FJ_CTR_PROBE_HITS], v);
+}
+
 // Step 2: every survivor of the first probe goes through the remaining
 // probes in order (R survivors per thread, their gathers issued together),
 // recording each entry in place, and then through the node's epilogue:
@@ -347,105 +539,333 @@ __global__ void __launch_bounds__(kThreads) k_scan_rest(const __grid_constant__ 
         if (b.mult) mult[r] = b.mult[idx[r]];
       }
     }
-    for (int p = 1; p < sc.n_probe && live; ++p) {
-      const ScanProbe& P = sc.probe[p];
-      c_probe += __popc(live);
-      live = scan_probe_rows<R>(P, s_mask[p], s_fon[p] ? P.filter : nullptr, live, row, e,
-                                b.mult ? mult : nullptr, &res->status);
-      c_hit += __popc(live);
-      if (!P.last)
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (live >> r & 1u) b.h[p][idx[r]] = e[r];
-    }
+    live = scan_rest_probes<R>(sc, b, s_mask, s_fon, live, idx, row, e, mult, &res->status,
+                               c_probe, c_hit);
     surv += __popc(live);
-    if (nd.mode == kModeItems) {
-      uint32_t pos = block_append(__popc(live), nd.out_n, &s_cnt, &s_base);
+    scan_epilogue<R>(nd, sc, b, atoms, res, idx, row, mult, live, &s_cnt, &s_base, s_min,
+                     my_count, any);
+  }
+  scan_block_totals(nd, res, s_min, s_red, my_count, any, surv, c_probe, c_hit);
+}
+
+// ---------------------------------------------------------------------------
+// Node 0 in one launch, for a cover without selections whose first probe is
+// one key column at the root of a narrow level (every binary2fj plan over a
+// star or chain of equi-joins).  Every warp works on its own, on a
+// contiguous run of tiles of 512 cover rows:
+//  * the cover's key column is streamed into the warp's shared memory by
+//    bulk asynchronous copies (TMA, two stages completing on mbarriers, the
+//    next tile in flight while this one is probed);
+//  * every row is tested against the first probe's Bloom filter (a
+//    multiplicative hash and one word), the rows that pass are queued, and
+//    the queue is resolved against the hash level with all 32 lanes busy;
+//  * survivors go to a region of the survivor buffer private to the warp
+//    (its own rows: no counter shared with other warps).
+// Then the warp runs the remaining probes breadth-first over its survivors:
+// one probe at a time over the whole list, compacting the hits in place
+// (each keeps the position it had after the first probe, where the entries
+// of every probe are recorded), and finally the epilogue.  No block-wide
+// barrier is taken before the final reduction, so the warps of an SM
+// overlap their latency chains.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t kFuseTile = 512;  // cover rows per warp tile (2 KB of keys)
+constexpr uint32_t kFuseStages = 2;
+constexpr size_t kFuseSmem = size_t(kThreads / 32) * kFuseTile * (kFuseStages * 4 + 2);
+constexpr uint32_t kSpinLimit = 50000;      // mbarrier waits before giving up
+constexpr uint32_t kSuspendHintNs = 20000;  // each wait sleeps at most this long
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+// Arm the barrier for `bytes` of asynchronous copies and copy them: global
+// [src, src + bytes) to shared [dst, dst + bytes).  src, dst and bytes are
+// multiples of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier to complete.  Each try suspends the
+// thread until the phase completes or kSuspendHintNs pass; false after
+// kSpinLimit tries (about a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// The rest of a narrow root lookup of `key` whose first slot `sl` (index h)
+// is loaded.
+__device__ __forceinline__ bool root1_resolve(const uint4* __restrict__ ht, uint32_t mask,
+                                              uint32_t key, uint32_t h, uint4 sl, uint32_t& e,
+                                              uint32_t& cnt) {
+  for (uint32_t it = 0; it <= mask; ++it) {
+    if (sl.x == key && sl.y == 0u) {
+      e = sl.z;
+      cnt = sl.w;
+      return true;
+    }
+    if (sl.x == kNone && sl.y == kNone) return false;
+    h = (h + 1) & mask;
+    sl = __ldg(&ht[h]);
+  }
+  return false;
+}
+
+// Bloom filter bits of one tile for lane `lane`: rows 128 g + 4 lane + i
+// (g < G, i < 4) map to bit 4 g + i.  FULL: all T rows exist and are staged
+// in `kt`; otherwise rows at or past `here` are absent and read from `kg`.
+template <uint32_t G, bool FULL>
+__device__ __forceinline__ uint32_t filter_bits(const int32_t* kt, const int32_t* kg,
+                                                uint32_t here, const uint32_t* filt,
+                                                uint32_t fw1, uint32_t lane) {
+  uint32_t pass = 0;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (!(live >> r & 1u)) continue;
-        uint32_t o = pos++;
-        if (o >= nd.out_cap) {
-          atomicOr(&res->status, kStItemsOverflow);
-          continue;
-        }
-        for (int k = 0; k < nd.n_out_vars; ++k)
-          nd.out_var[k][o] = src_value(nd.src[nd.out_var_id[k]], 0, row[r]);
-        for (int a = 0; a < FJ_MAX_ATOMS; ++a)
-          if (nd.out_h[a]) nd.out_h[a][o] = scan_handle(sc, b, nd.out_h_src[a], idx[r]);
-        if (nd.out_mult) nd.out_mult[o] = mult[r];
+  for (uint32_t g = 0; g < G; ++g) {
+    const uint32_t j0 = g * 128 + 4 * lane;
+    int32_t k[4];
+    if (FULL) {
+      int4 v = *reinterpret_cast<const int4*>(&kt[j0]);
+      k[0] = v.x;
+      k[1] = v.y;
+      k[2] = v.z;
+      k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) k[i] = j0 + i < here ? __ldg(kg + j0 + i) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      bool ok = FULL || j0 + i < here;
+      if (filt) {
+        const uint32_t fh = filter_hash_root1(k[i]);
+        const uint32_t m = bloom_bits(fh);
+        ok = ok && (__ldg(&filt[fh & fw1]) & m) == m;
       }
-    } else if (nd.mode == kModeAggregate) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (!(live >> r & 1u)) continue;
-        uint64_t m = mult[r];
-        for (int t = 0; t < nd.n_tail && m; ++t) {
-          const TailDev& td = nd.tail[t];
-          const AtomDev& ta = atoms[td.atom];
-          m = mul_sat(m, ta.L[td.lvl].count[scan_handle(sc, b, td.hsrc, idx[r])], &res->status);
-        }
-        if (!m) continue;
-        unsigned long long before = my_count;
-        my_count += m;
-        if (my_count < before) atomicOr(&res->status, kStCountOverflow);
-        any = true;
-        for (int k = 0; k < nd.n_min; ++k)
-          atomicMin(&s_min[nd.min_idx[k]], src_value(nd.src[nd.min_var[k]], 0, row[r]));
-        for (int t = 0; t < nd.n_tail; ++t) {
-          const TailDev& td = nd.tail[t];
-          if (!td.n_min) continue;
-          const AtomDev& ta = atoms[td.atom];
-          uint32_t h = scan_handle(sc, b, td.hsrc, idx[r]);
-          uint32_t bg = ta.L[td.lvl].begin[h], cn = ta.L[td.lvl].count[h];
-          for (int k = 0; k < td.n_min; ++k) {
-            const int32_t* col = ta.cols[td.min_col[k]];
-            int32_t lo = INT32_MAX;
-            for (uint32_t x = 0; x < cn; ++x) lo = min(lo, col[ta.perm[bg + x]]);
-            atomicMin(&s_min[td.min_idx[k]], lo);
-          }
-        }
-      }
-    } else {  // kModeMaterialize
-      uint64_t tot = 0;
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (live >> r & 1u) tot += mult[r];
-      uint64_t inc = warp_incl_scan<unsigned long long>(tot);
-      uint64_t base = 0;
-      if (lane_id() == 31 && inc) base = atomicAdd(&res->n_out, (unsigned long long)inc);
-      base = __shfl_sync(0xffffffffu, (unsigned long long)base, 31) + inc - tot;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (!(live >> r & 1u)) continue;
-        for (uint64_t x = 0; x < mult[r]; ++x) {
-          uint64_t orow = base++;
-          if (orow >= nd.out_rows_cap) {
-            atomicOr(&res->status, kStOutputOverflow);
-            continue;
-          }
-          for (int h = 0; h < nd.n_head; ++h)
-            nd.out_tuples[orow * nd.n_head + h] = src_value(nd.src[nd.head_var[h]], 0, row[r]);
-        }
-      }
+      if (ok) pass |= 1u << (4 * g + i);
     }
   }
-  if (nd.mode == kModeAggregate) {
-    unsigned long long tot = block_sum<unsigned long long>(my_count, s_red);
-    int any_b = __syncthreads_or(any);
-    if (threadIdx.x == 0 && tot) {
-      unsigned long long old = atomicAdd(&res->count, tot);
-      if (old + tot < old) atomicOr(&res->status, kStCountOverflow);
-    }
-    if (any_b && threadIdx.x < FJ_MAX_VARS)
-      atomicMin(&res->mins[threadIdx.x], s_min[threadIdx.x]);
+  return pass;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constant__ NodeDev nd,
+                                                            const __grid_constant__ ScanDev sc,
+                                                            AtomDev* atoms, ResultDev* res) {
+  constexpr uint32_t T = kFuseTile, NS = kFuseStages, W = kThreads / 32;
+  constexpr uint32_t G = T / 128;  // groups of 4 rows per lane
+  static_assert(G <= 8, "a lane's pass mask holds 32 rows");
+  constexpr int QU = 2;  // queue entries per lane with slot loads in flight
+  constexpr int U = 4;   // list entries per lane per round of a later probe
+  // Dynamic shared memory (kFuseSmem bytes): per warp NS key stages of T
+  // rows, then per warp the queue of the rows of a tile that pass the filter.
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  auto s_keys = reinterpret_cast<int32_t(*)[NS][T]>(s_dyn);
+  auto s_q = reinterpret_cast<uint16_t(*)[T]>(s_dyn + size_t(W) * NS * T * 4);
+  __shared__ alignas(8) uint64_t s_bar[W][NS];
+  __shared__ uint32_t s_mask[FJ_MAX_SUB], s_fon[FJ_MAX_SUB];
+  __shared__ int32_t s_min[FJ_MAX_VARS];
+  __shared__ unsigned long long s_red[33];
+  __shared__ uint32_t s_cnt, s_base;
+  const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+  const uint64_t begin = nd.chunk_begin;
+  const uint32_t n_rows = uint32_t(nd.chunk_end - begin);
+  const uint32_t n_tiles = (n_rows + T - 1) / T;
+  const uint32_t n_warps = gridDim.x * W, gw = blockIdx.x * W + warp;
+  // Balanced contiguous runs: warp gw takes tiles [gw n / N, (gw + 1) n / N).
+  const uint32_t t0 = uint32_t(uint64_t(gw) * n_tiles / n_warps);
+  const uint32_t t1 = uint32_t(uint64_t(gw + 1) * n_tiles / n_warps);
+  const uint32_t region = t0 * T;
+  const ScanProbe& P = sc.probe[0];
+  const int32_t* kcol = P.kcol[0] + begin;
+  const ScanBuf& out = sc.buf[0];
+  int32_t(*keys)[T] = s_keys[warp];
+  uint64_t* bar = s_bar[warp];
+  uint16_t* q = s_q[warp];
+
+  if (tid < uint32_t(sc.n_probe)) {
+    s_mask[tid] = *sc.probe[tid].mask;
+    s_fon[tid] = sc.probe[tid].filter ? *sc.probe[tid].filter_on : 0u;
   }
-  unsigned long long v = block_sum<unsigned long long>(surv, s_red);
-  if (threadIdx.x == 0 && v) atomicAdd(&res->ctr[FJ_CTR_SURVIVORS], v);
-  v = block_sum<unsigned long long>(c_probe, s_red);
-  if (threadIdx.x == 0 && v) atomicAdd(&res->ctr[FJ_CTR_PROBES], v);
-  v = block_sum<unsigned long long>(c_hit, s_red);
-  if (threadIdx.x == 0 && v) atomicAdd(&res->ctr[FJ_CTR_PROBE_HITS], v);
+  if (tid < FJ_MAX_VARS) s_min[tid] = INT32_MAX;
+  if (tid == 0) s_cnt = 0;
+  if (lane == 0) {
+    for (uint32_t i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // Lane 0 is the warp's producer: its first NS full tiles now, then each
+  // tile NS ahead once the warp is done with the stage it reuses.
+  if (lane == 0)
+    for (uint32_t t = t0; t < t1 && t < t0 + NS; ++t)
+      if ((t + 1) * T <= n_rows) tma_load_1d(keys[t - t0], kcol + size_t(t) * T, T * 4, &bar[t - t0]);
+
+  const uint32_t mask = s_mask[0];
+  const uint32_t* filt = s_fon[0] ? P.filter : nullptr;
+  const uint32_t fw1 = P.filter_words - 1;
+  const bool keep_h = !P.last;
+  unsigned long long c_probe = 0, c_hit = 0, my_count = 0, surv = 0;
+  bool any = false, timed_out = false;
+  uint32_t n_surv = 0;  // survivors in the warp's region (the same in every lane)
+  uint32_t t = t0;
+  for (; t < t1; ++t) {
+    const uint32_t li = t - t0, st = li % NS;
+    const uint32_t here = min(T, n_rows - t * T);
+    const bool staged = here == T;
+    if (staged && !mbar_wait(&bar[st], (li / NS) & 1u)) timed_out = true;
+    if (__any_sync(0xffffffffu, timed_out)) break;
+    const int32_t* kt = keys[st];
+    const int32_t* kg = kcol + size_t(t) * T;
+    const uint32_t pass = staged ? filter_bits<G, true>(kt, kg, here, filt, fw1, lane)
+                                 : filter_bits<G, false>(kt, kg, here, filt, fw1, lane);
+    if (lane == 0) c_probe += here;
+    const uint32_t np = __popc(pass);
+    const uint32_t incl = warp_incl_scan(np);
+    const uint32_t qn = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t qp = incl - np;
+    for (uint32_t m = pass; m; m &= m - 1) {
+      const uint32_t bt = __ffs(m) - 1;
+      q[qp++] = uint16_t((bt >> 2) * 128 + 4 * lane + (bt & 3));
+    }
+    __syncwarp();
+    // Resolve the queue, QU entries per lane with their first slot loads in
+    // flight together; hits are appended to the warp's region.
+    const uint32_t rbase = uint32_t(begin + size_t(t) * T);
+    for (uint32_t i0 = 0; i0 < qn; i0 += QU * 32) {
+      uint32_t key[QU], hh[QU], jj[QU];
+      uint4 sl[QU];
+#pragma unroll
+      for (int u = 0; u < QU; ++u) {
+        const uint32_t i = i0 + u * 32 + lane;
+        jj[u] = i < qn ? q[i] : 0u;
+        key[u] = uint32_t(staged ? kt[jj[u]] : __ldg(kg + jj[u]));
+        hh[u] = hash_root1(int32_t(key[u])) & mask;
+        if (i < qn) sl[u] = __ldg(&P.ht[hh[u]]);
+      }
+#pragma unroll
+      for (int u = 0; u < QU; ++u) {
+        uint32_t e = 0, cnt = 0;
+        const bool hit = i0 + u * 32 + lane < qn &&
+                         root1_resolve(P.ht, mask, key[u], hh[u], sl[u], e, cnt);
+        const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const uint32_t pos = region + n_surv + __popc(hm & lanemask_lt());
+          out.row[pos] = rbase + jj[u];
+          if (keep_h) out.h[0][pos] = e;
+          if (out.mult) out.mult[pos] = P.last ? cnt : 1u;
+        }
+        n_surv += __popc(hm);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && t + NS < t1 && (t + NS + 1) * T <= n_rows)
+      tma_load_1d(keys[st], kcol + size_t(t + NS) * T, T * 4, &bar[st]);
+  }
+  if (t < t1) {
+    // A copy did not complete in time: record it and let the warp's copies
+    // still in flight land (bounded again) before its shared memory can be
+    // released; the host reports the error.
+    if (lane == 0) {
+      atomicOr(&res->status, kStTimeout);
+      for (uint32_t u = t; u < t1 && u < t + NS; ++u)
+        if ((u + 1) * T <= n_rows) mbar_wait(&bar[(u - t0) % NS], ((u - t0) / NS) & 1u);
+    }
+    n_surv = 0;
+  }
+  if (lane == 0) c_hit += n_surv;
+
+  // Remaining probes, breadth-first over the warp's list [region, region+n).
+  uint32_t n_list = n_surv;
+  for (int p = 1; p < sc.n_probe && n_list; ++p) {
+    const ScanProbe& Pp = sc.probe[p];
+    const uint32_t mp = s_mask[p];
+    const uint32_t* fp = s_fon[p] ? Pp.filter : nullptr;
+    uint32_t n_out = 0;
+    for (uint32_t i0 = 0; i0 < n_list; i0 += U * 32) {
+      uint32_t row[U], e[U], src0[U];
+      uint64_t mult[U];
+      uint32_t lv = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = i0 + u * 32 + lane, pos = region + i;
+        row[u] = 0;
+        src0[u] = pos;
+        mult[u] = 1;
+        if (i < n_list) {
+          lv |= 1u << u;
+          row[u] = out.row[pos];
+          if (p > 1) src0[u] = out.src[pos];
+          if (out.mult) mult[u] = out.mult[pos];
+        }
+      }
+      c_probe += __popc(lv);
+      lv = scan_probe_rows<U>(Pp, mp, fp, lv, row, e, out.mult ? mult : nullptr, &res->status);
+      c_hit += __popc(lv);
+      __syncwarp();  // every lane has read its entries before any is rewritten
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool hit = lv >> u & 1u;
+        const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const uint32_t pos = region + n_out + __popc(hm & lanemask_lt());
+          if (!Pp.last) out.h[p][src0[u]] = e[u];
+          out.row[pos] = row[u];
+          out.src[pos] = src0[u];
+          if (out.mult) out.mult[pos] = mult[u];
+        }
+        n_out += __popc(hm);
+      }
+    }
+    n_list = n_out;
+  }
+  // Epilogue over the final list.
+  for (uint32_t i0 = 0; i0 < n_list; i0 += uint32_t(R) * 32) {
+    uint32_t idx[R], row[R];
+    uint64_t mult[R];
+    uint32_t lv = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = i0 + r * 32 + lane, pos = region + i;
+      idx[r] = pos;
+      row[r] = 0;
+      mult[r] = 1;
+      if (i < n_list) {
+        lv |= 1u << r;
+        row[r] = out.row[pos];
+        if (sc.n_probe > 1) idx[r] = out.src[pos];
+        if (out.mult) mult[r] = out.mult[pos];
+      }
+    }
+    surv += __popc(lv);
+    scan_epilogue<R, true>(nd, sc, out, atoms, res, idx, row, mult, lv, &s_cnt, &s_base, s_min,
+                           my_count, any);
+  }
+  scan_block_totals(nd, res, s_min, s_red, my_count, any, surv, c_probe, c_hit);
+  if (blockIdx.x == 0 && tid == 0 && n_rows)
+    atomicAdd(&res->ctr[FJ_CTR_COVER_ITERS], (unsigned long long)n_rows);
 }
 
 // The survivor count to zero before a chunk.
