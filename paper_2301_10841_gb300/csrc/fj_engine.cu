@@ -168,6 +168,8 @@ struct fj_prepared {
   bool scan0 = false;
   ScanDev sc0{};
   int fuse_blocks = 0;  // > 0: node 0 runs as one k_scan_fused launch of this many blocks
+  RootsState* roots_state = nullptr;  // k_force_roots barrier
+  int roots_grid = 0;                 // > 0: root-only forces run as one cooperative launch
   uint64_t kernels = 0;
   uint64_t chunks = 0;
   bool explicit_built = false;  // levels built outside the join since reset
@@ -223,6 +225,17 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
   cudaStream_t s = c->stream;
   ForceJobs fj{P->d_atoms, d_jobs, n_jobs};
   cudaEvent_t t0 = P->timing() ? P->mark() : nullptr;
+  if (roots && P->roots_grid > 0) {
+    CK(cudaMemsetAsync(P->roots_state, 0, sizeof(RootsState), s));
+    RootsState* cs = P->roots_state;
+    ResultDev* rd = c->d_res;
+    void* args[] = {&fj, &cs, &rd};
+    CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_force_roots),
+                                   dim3(P->roots_grid), dim3(kRootThreads), args, 0, s));
+    P->kernels += 1;
+    if (t0) P->t_build.emplace_back(t0, P->mark());
+    return;
+  }
   int cap = c->n_sm * 8;
   int g_rows = blocks_for(ub_rows, kThreads * 4, cap);
   int g_ht = blocks_for(uint64_t(ub_rows) * 2 + 2, kThreads * 4, cap);
@@ -863,6 +876,21 @@ static void setup_scan(fj_prepared* P) {
   }
 }
 
+// Root-only forces as one cooperative launch: every block resident (two
+// blocks of 512 threads per SM at most), where the device supports
+// cooperative launches.
+static void setup_roots(fj_prepared* P) {
+  P->roots_grid = 0;
+  int coop = 0;
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, P->ctx->device));
+  if (!coop) return;
+  int b = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force_roots, kRootThreads, 0));
+  if (b < 1) return;
+  P->roots_state = P->alloc<RootsState>(1);
+  P->roots_grid = P->ctx->n_sm * std::min(b, 2);
+}
+
 static void ensure_output(fj_prepared* P, uint64_t rows) {
   if (!P->materialize) return;
   int nh = int(P->q.head.size());
@@ -1058,6 +1086,7 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
     upload_atoms(P.get(), query);
     finalize_nodes(P.get());
     setup_scan(P.get());
+    setup_roots(P.get());
     reset_state(P.get(), true);
   } catch (...) {
     for (void* p : P->allocs) dfree(ctx, p);

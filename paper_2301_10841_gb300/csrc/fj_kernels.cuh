@@ -702,4 +702,527 @@ __global__ void k_force_reset_req(ForceJobs fj) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Root levels in one cooperative launch.  Forcing the root of an atom (its
+// first schema level) reads the whole base table; for a node whose jobs are
+// all roots, the passes of a force run in one kernel whose blocks are all
+// resident (cudaLaunchCooperativeKernel), separated by grid barriers:
+//   A  compact the rows that pass the selection,
+//   B  size and clear each table and filter,
+//   C  insert the keys, count rows per key, list the new keys,
+//   D  give each new key its entry and its range of offsets,
+//   E  scatter the offsets,
+//   F  reset the fill cursors and record the level as forced.
+// Each pass splits the work of all jobs into one contiguous range per block
+// and takes several independent elements per thread at a time (the passes
+// are chains of dependent L2 accesses); offsets come from one counter per
+// job, advanced once per block and job in A, once per 2048 elements in C
+// and D.  Every barrier wait is bounded: on expiry the kernel sets
+// kStTimeout and its blocks return; the host reports FJ_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+
+constexpr int kRootThreads = 512;
+
+struct RootsState {        // zeroed before each launch
+  unsigned int bar_count;  // blocks arrived at the current barrier
+  unsigned int bar_gen;    // barriers completed
+  unsigned int n_pass[FJ_MAX_ATOMS];
+  unsigned int n_new[FJ_MAX_ATOMS];
+};
+
+constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about a second)
+
+// Grid-wide barrier among all blocks of a cooperative launch.  Returns false
+// (in every thread of the block) when the wait ran out.
+__device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &cs->bar_gen;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    if (atomicAdd(&cs->bar_count, 1u) == gridDim.x - 1) {
+      cs->bar_count = 0;
+      __threadfence();
+      atomicAdd(&cs->bar_gen, 1u);
+    } else {
+      uint32_t it = 0;
+      while (*vgen == gen) {
+        if (++it > kGridSpinLimit) {
+          atomicOr(status, kStTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok);
+}
+
+// s_off[0..n] = prefix sums of size(j) over the jobs; all threads call it.
+template <typename F>
+__device__ __forceinline__ void jobs_prefix(int n, uint32_t* s_off, F size) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int j = 0; j < n; ++j) {
+      s_off[j] = acc;
+      acc += size(j);
+    }
+    s_off[n] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int job_at(const uint32_t* s_off, int n, uint32_t x) {
+  int j = 0;
+  while (j + 1 < n && s_off[j + 1] <= x) ++j;
+  return j;
+}
+
+// This block's contiguous part [lo, hi) of `total` elements.
+__device__ __forceinline__ void block_range(uint32_t total, uint32_t& lo, uint32_t& hi) {
+  lo = uint32_t(uint64_t(total) * blockIdx.x / gridDim.x);
+  hi = uint32_t(uint64_t(total) * (blockIdx.x + 1) / gridDim.x);
+}
+
+// A root job's descriptors, copied once into shared memory so the passes
+// do not chase the atom descriptors in global memory per element.
+struct RootJob {
+  uint4* ht;
+  uint32_t* filter;
+  uint32_t filter_words;
+  uint32_t ht_cap_max;
+  const int32_t* kc[3];
+  int nk;
+  int wide;
+  int ident;     // rows are the base table's, filtered by the selection
+  int act;       // the level is requested and not yet built
+  uint32_t src;  // rows to read (base table, or perm[0, n_pass))
+  uint32_t base_e;
+  uint32_t* tmp_row;
+  uint32_t* tmp_slot;
+  uint32_t* newslots;
+  uint32_t* perm;
+  uint64_t* key;
+  uint32_t* count;
+  uint32_t* begin;
+  uint32_t* fill;
+  uint32_t* cstate;
+  uint32_t* cfirst;
+  uint32_t* cnkeys;
+  uint32_t* pfill;  // the root's fill cursor
+  float load;
+  int n_preds;
+  const int32_t* pcol[FJ_MAX_PREDS];
+  int pop[FJ_MAX_PREDS];
+  int32_t pval[FJ_MAX_PREDS];
+};
+
+__device__ __forceinline__ bool pred_holds(int op, int32_t v, int32_t c) {
+  switch (op) {
+    case FJ_LT: return v < c;
+    case FJ_LE: return v <= c;
+    case FJ_GT: return v > c;
+    case FJ_GE: return v >= c;
+    case FJ_EQ: return v == c;
+    default: return v != c;
+  }
+}
+
+// Pass bits of rows r0 + k * blockDim + tid (k < RPT, below r1) of a root
+// job.
+template <int RPT>
+__device__ __forceinline__ uint32_t root_rows_pass(const RootJob& J, uint32_t r0, uint32_t r1,
+                                                   uint32_t (&row)[RPT]) {
+  uint32_t pass = 0;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const uint32_t i = r0 + k * blockDim.x + threadIdx.x;
+    row[k] = i;
+    if (i < r1) {
+      if (!J.ident) row[k] = J.perm[i];
+      pass |= 1u << k;
+    }
+  }
+  if (J.ident) {
+    // One selection at a time, its column for all the rows at once.
+    for (int p = 0; p < J.n_preds; ++p) {
+      int32_t v[RPT];
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) v[k] = (pass >> k & 1u) ? __ldg(J.pcol[p] + row[k]) : 0;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k)
+        if ((pass >> k & 1u) && !pred_holds(J.pop[p], v[k], J.pval[p])) pass &= ~(1u << k);
+    }
+  }
+  return pass;
+}
+
+// Insert a narrow key: a compare-and-swap at its home slot `h` was
+// answered with `old`; continue probing after it when the slot holds
+// another key.
+__device__ __forceinline__ uint32_t ht_insert_from(uint4* ht, uint32_t mask, uint64_t kw,
+                                                   uint32_t h, unsigned long long old,
+                                                   bool& claimed, uint32_t* status) {
+  claimed = false;
+  for (uint32_t it = 0; it <= mask; ++it) {
+    if (old == kEmptyKey) {
+      claimed = true;
+      return h;
+    }
+    if (old == kw) return h;
+    h = (h + 1) & mask;
+    old = atomicCAS(slot_key(ht, h), kEmptyKey, kw);
+  }
+  atomicOr(status, kStTableFull);
+  return kNone;
+}
+
+__global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, RootsState* cs,
+                                                                 ResultDev* res) {
+  constexpr int E = 4;  // independent elements per thread in C, D and E
+  constexpr uint32_t NT = kRootThreads;
+  const int nj = fj.n_jobs;
+  const uint32_t tid = threadIdx.x;
+  __shared__ RootJob s_job[FJ_MAX_ATOMS];
+  __shared__ uint32_t s_off[FJ_MAX_ATOMS + 1];
+  __shared__ uint32_t s_mask[FJ_MAX_ATOMS], s_fon[FJ_MAX_ATOMS];
+  __shared__ uint32_t s_np[FJ_MAX_ATOMS], s_nn[FJ_MAX_ATOMS];  // rows passing, new keys
+  __shared__ uint32_t s_scan[33];
+  __shared__ uint32_t s_base;
+  if (tid < uint32_t(nj)) {
+    const int2 jb = fj.jobs[tid];
+    const AtomDev& a = fj.atoms[jb.x];
+    const LevelDev& L = a.L[jb.y];
+    const LevelDev& P = a.L[jb.y - 1];
+    RootJob& J = s_job[tid];
+    J.ht = L.ht;
+    J.filter = L.filter;
+    J.filter_words = L.filter_words;
+    J.ht_cap_max = L.ht_cap_max;
+    J.nk = L.nk;
+    for (int k = 0; k < 3; ++k) J.kc[k] = a.cols[L.kcol[k]];
+    J.wide = L.wide;
+    J.ident = !a.root_mat;
+    J.act = L.n_req > 0 && !L.cleared;
+    J.src = a.root_mat ? a.n_pass : a.n_rows;
+    J.base_e = L.n_entries;
+    J.tmp_row = a.tmp_row;
+    J.tmp_slot = a.tmp_slot;
+    J.newslots = a.newslots;
+    J.perm = a.perm;
+    J.key = L.key;
+    J.count = L.count;
+    J.begin = L.begin;
+    J.fill = L.fill;
+    J.cstate = L.child_state;
+    J.cfirst = L.child_first;
+    J.cnkeys = L.child_nkeys;
+    J.pfill = P.fill;
+    J.load = a.load > 0.f ? a.load : 0.5f;
+    J.n_preds = a.n_preds;
+    for (int p = 0; p < a.n_preds; ++p) {
+      J.pcol[p] = a.cols[a.pred_col[p]];
+      J.pop[p] = a.pred_op[p];
+      J.pval[p] = a.pred_val[p];
+    }
+  }
+  uint32_t lo, hi;
+
+  // A: rows that pass the selection, compacted into tmp_row, 16 rows per
+  // thread per sweep of the block's part of a job (one counter advance per
+  // sweep).  One-column narrow keys travel with the row (in tmp_slot until
+  // C replaces them by the slot), read while the rows are at hand.
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_job[j].src : 0u; });
+  block_range(s_off[nj], lo, hi);
+  for (int j = 0; j < nj; ++j) {
+    const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
+    if (a0 >= a1) continue;
+    const RootJob& J = s_job[j];
+    const bool k1 = !J.wide && J.nk == 1;
+    const uint32_t r1 = a1 - s_off[j];
+    for (uint32_t r = a0 - s_off[j]; r < r1; r += 16 * NT) {
+      uint32_t row[16];
+      const uint32_t pass = root_rows_pass<16>(J, r, r1, row);
+      int32_t key[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) key[k] = (k1 && (pass >> k & 1u)) ? __ldg(J.kc[0] + row[k]) : 0;
+      uint32_t tot;
+      uint32_t o = block_excl_scan<uint32_t>(__popc(pass), s_scan, &tot);
+      if (tid == 0) s_base = tot ? atomicAdd(&cs->n_pass[j], tot) : 0u;
+      __syncthreads();
+      o += s_base;
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (pass >> k & 1u) {
+          J.tmp_row[o] = row[k];
+          if (k1) J.tmp_slot[o] = uint32_t(key[k]);
+          ++o;
+        }
+      __syncthreads();
+    }
+  }
+  if (!grid_sync(cs, &res->status)) return;
+  if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[tid];
+  __syncthreads();
+
+  // B: size each table for its passing rows; clear table and filter.
+  if (tid < uint32_t(nj)) {
+    const RootJob& J = s_job[tid];
+    const uint32_t n_in = s_np[tid];
+    const float want = float(n_in) / J.load;
+    uint32_t cap = 16;
+    while (float(cap) < want && cap < J.ht_cap_max) cap <<= 1;
+    s_mask[tid] = cap - 1;
+    s_fon[tid] = J.filter && uint64_t(n_in) * 4 <= uint64_t(J.filter_words) * 32;
+    if (blockIdx.x == 0 && J.act) {
+      LevelDev& L = fj.atoms[fj.jobs[tid].x].L[fj.jobs[tid].y];
+      L.mask = cap - 1;
+      L.filter_on = s_fon[tid];
+      L.n_in = n_in;
+    }
+  }
+  jobs_prefix(nj, s_off, [&](int j) {
+    const RootJob& J = s_job[j];
+    if (!J.act) return 0u;
+    return (s_mask[j] + 2) * (J.wide ? 2u : 1u) + (s_fon[j] ? J.filter_words / 4 : 0u);
+  });
+  for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
+    const int j = job_at(s_off, nj, x);
+    const RootJob& J = s_job[j];
+    const uint32_t u = x - s_off[j], ns = (s_mask[j] + 2) * (J.wide ? 2u : 1u);
+    if (u < ns) {
+      if (J.wide)
+        J.ht[u] = (u & 1u) ? make_uint4(kNone, 0u, 0u, 0u) : make_uint4(kNone, kNone, kNone, kNone);
+      else
+        J.ht[u] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
+    } else {
+      reinterpret_cast<uint4*>(J.filter)[u - ns] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  if (!grid_sync(cs, &res->status)) return;
+
+  // C: insert every passing row's key (E per thread, their first
+  // compare-and-swaps in flight together) and count rows per key; list the
+  // new keys (their position in the list is their index under the root).
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
+  block_range(s_off[nj], lo, hi);
+  for (int j = 0; j < nj; ++j) {
+    const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
+    if (a0 >= a1) continue;
+    const RootJob& J = s_job[j];
+    const uint32_t mask = s_mask[j];
+    for (uint32_t r = a0 - s_off[j]; r < a1 - s_off[j]; r += E * NT) {
+      const uint32_t r1 = a1 - s_off[j];
+      uint32_t slot[E];
+      uint32_t claimed = 0;
+      if (!J.wide) {
+        uint64_t kw[E];
+        uint32_t h[E];
+        unsigned long long old[E];
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          const uint32_t i = r + u * NT + tid;
+          kw[u] = 0;
+          if (i >= r1) continue;
+          if (J.nk == 1) {
+            kw[u] = J.tmp_slot[i];
+          } else {
+            const uint32_t row = J.tmp_row[i];
+            kw[u] = pack_key(0u, J.nk, J.nk > 0 ? __ldg(J.kc[0] + row) : 0,
+                             J.nk > 1 ? __ldg(J.kc[1] + row) : 0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          const uint32_t i = r + u * NT + tid;
+          if (i >= r1 || kw[u] == kEmptyKey) continue;
+          h[u] = hash_key(kw[u]) & mask;
+          old[u] = atomicCAS(slot_key(J.ht, h[u]), kEmptyKey, kw[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          const uint32_t i = r + u * NT + tid;
+          slot[u] = kNone;
+          if (i >= r1) continue;
+          bool cl = false;
+          if (kw[u] == kEmptyKey)
+            slot[u] = ht_insert(J.ht, mask, kw[u], cl, &res->status);
+          else
+            slot[u] = ht_insert_from(J.ht, mask, kw[u], h[u], old[u], cl, &res->status);
+          if (cl && s_fon[j]) {
+            const uint32_t fh = filter_hash(kw[u]);
+            atomicOr(&J.filter[fh & (J.filter_words - 1)], bloom_bits(fh));
+          }
+          if (cl) claimed |= 1u << u;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          const uint32_t i = r + u * NT + tid;
+          slot[u] = kNone;
+          if (i >= r1) continue;
+          const uint32_t row = J.tmp_row[i];
+          uint4 kw = make_uint4(0u, J.nk > 0 ? uint32_t(__ldg(J.kc[0] + row)) : 0u,
+                                J.nk > 1 ? uint32_t(__ldg(J.kc[1] + row)) : 0u,
+                                J.nk > 2 ? uint32_t(__ldg(J.kc[2] + row)) : 0u);
+          bool cl = false;
+          slot[u] = ht_insert_wide(J.ht, mask, kw, cl, &res->status);
+          if (cl) claimed |= 1u << u;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < E; ++u) {
+        const uint32_t i = r + u * NT + tid;
+        if (i >= r1) continue;
+        if (slot[u] != kNone) atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u);
+        J.tmp_slot[i] = slot[u];
+      }
+      uint32_t tot;
+      uint32_t pos = block_excl_scan<uint32_t>(__popc(claimed), s_scan, &tot);
+      if (tid == 0) s_base = tot ? atomicAdd(&cs->n_new[j], tot) : 0u;
+      __syncthreads();
+      pos += s_base;
+#pragma unroll
+      for (int u = 0; u < E; ++u) {
+        if (!(claimed >> u & 1u)) continue;
+        J.newslots[pos] = slot[u];
+        *slot_e(J.ht, J.wide, slot[u]) = pos;
+        ++pos;
+      }
+    }
+  }
+  if (!grid_sync(cs, &res->status)) return;
+  if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[tid];
+  __syncthreads();
+
+  // D: entries of the new keys, each with its range inside the root's range
+  // (one advance of the root's fill cursor per E * blockDim keys).
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_nn[j] : 0u; });
+  block_range(s_off[nj], lo, hi);
+  for (int j = 0; j < nj; ++j) {
+    const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
+    if (a0 >= a1) continue;
+    const RootJob& J = s_job[j];
+    for (uint32_t r = a0 - s_off[j]; r < a1 - s_off[j]; r += E * NT) {
+      const uint32_t r1 = a1 - s_off[j];
+      uint32_t s[E], cnt[E], sum = 0;
+      uint64_t kw[E];
+#pragma unroll
+      for (int u = 0; u < E; ++u) {
+        const uint32_t i = r + u * NT + tid;
+        s[u] = i < r1 ? J.newslots[i] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < E; ++u) {
+        const uint32_t i = r + u * NT + tid;
+        cnt[u] = 0;
+        kw[u] = 0;
+        if (i >= r1) continue;
+        if (J.wide) {
+          kw[u] = 0;  // wide entries keep only the parent (the root: 0)
+          cnt[u] = J.ht[2 * size_t(s[u]) + 1].y;
+        } else {
+          const uint4 sl = J.ht[s[u]];
+          kw[u] = s[u] == s_mask[j] + 1 ? kEmptyKey : ((uint64_t(sl.y) << 32) | sl.x);
+          cnt[u] = sl.w;
+        }
+        sum += cnt[u];
+      }
+      uint32_t tot;
+      uint32_t b = block_excl_scan<uint32_t>(sum, s_scan, &tot);
+      if (tid == 0) s_base = tot ? atomicAdd(J.pfill, tot) : 0u;
+      __syncthreads();
+      b += s_base;  // the root's range starts at 0 (identity) or is all of perm
+#pragma unroll
+      for (int u = 0; u < E; ++u) {
+        const uint32_t i = r + u * NT + tid;
+        if (i >= r1) continue;
+        const uint32_t e = J.base_e + i;
+        *slot_e(J.ht, J.wide, s[u]) = e;
+        J.key[e] = kw[u];
+        J.count[e] = cnt[u];
+        J.begin[e] = b;
+        J.fill[e] = b;
+        if (J.cstate) J.cstate[e] = kUnforced;
+        if (J.cnkeys) J.cnkeys[e] = 0;
+        if (J.cfirst) J.cfirst[e] = 0;
+        b += cnt[u];
+      }
+    }
+  }
+  if (!grid_sync(cs, &res->status)) return;
+
+  // E: every passing row to its entry's range.
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
+  for (uint32_t x0 = blockIdx.x * E * NT; x0 < s_off[nj]; x0 += gridDim.x * E * NT) {
+    uint32_t t[E], e[E];
+    int jj[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      const uint32_t x = x0 + u * NT + tid;
+      t[u] = kNone;
+      jj[u] = 0;
+      if (x >= s_off[nj]) continue;
+      jj[u] = job_at(s_off, nj, x);
+      t[u] = s_job[jj[u]].tmp_slot[x - s_off[jj[u]]];
+    }
+#pragma unroll
+    for (int u = 0; u < E; ++u)
+      if (t[u] != kNone) e[u] = *slot_e(s_job[jj[u]].ht, s_job[jj[u]].wide, t[u]);
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      if (t[u] == kNone) continue;
+      const RootJob& J = s_job[jj[u]];
+      J.perm[atomicAdd(&J.fill[e[u]], 1u)] = J.tmp_row[x0 + u * NT + tid - s_off[jj[u]]];
+    }
+  }
+  if (!grid_sync(cs, &res->status)) return;
+
+  // F: fill cursors back to zero (the next level's bump allocation), and
+  // the level's bookkeeping.
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_nn[j] : 0u; });
+  for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
+    const int j = job_at(s_off, nj, x);
+    s_job[j].fill[s_job[j].base_e + x - s_off[j]] = 0;
+  }
+  if (blockIdx.x == 0 && tid < uint32_t(nj)) {
+    const int j = tid;
+    const RootJob& J = s_job[j];
+    AtomDev& a = fj.atoms[fj.jobs[j].x];
+    LevelDev& L = a.L[fj.jobs[j].y];
+    LevelDev& P = a.L[fj.jobs[j].y - 1];
+    if (!J.act) {  // nothing to build: the request list starts empty again
+      L.n_req = 0;
+      L.n_in = 0;
+      return;
+    }
+    const uint32_t np = s_np[j], nn = s_nn[j];
+    for (uint32_t r = 0; r < L.n_req; ++r) P.child_state[L.req[r]] = kForced;
+    P.child_first[0] = J.base_e;
+    P.child_nkeys[0] = nn;
+    if (J.ident) {
+      a.n_pass = np;
+      a.root_mat = 1;
+      P.begin[0] = 0;
+      P.count[0] = np;
+    }
+    atomicAdd(&res->ctr[FJ_CTR_ROOTS_BUILT], 1ull);
+    atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
+             1ull << fj.jobs[j].x);
+    atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)np);
+    L.n_rows = J.src;
+    L.n_tmp = np;
+    L.n_new = nn;
+    L.base = J.base_e;
+    L.n_entries = J.base_e + nn;
+    L.cleared = 1;
+    L.n_req = 0;
+    L.n_in = 0;
+  }
+}
+
 }  // namespace fj
