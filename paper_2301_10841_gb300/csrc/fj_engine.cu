@@ -226,8 +226,7 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
   ForceJobs fj{P->d_atoms, d_jobs, n_jobs};
   cudaEvent_t t0 = P->timing() ? P->mark() : nullptr;
   if (roots && P->roots_grid > 0) {
-    CK(cudaMemsetAsync(P->roots_state, 0, sizeof(RootsState), s));
-    RootsState* cs = P->roots_state;
+    RootsState* cs = P->roots_state;  // zero: set by k_reset, left so by each launch
     ResultDev* rd = c->d_res;
     void* args[] = {&fj, &cs, &rd};
     CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_force_roots),
@@ -453,7 +452,7 @@ static void compile(fj_prepared* P) {
     }
 
   // Atom device descriptors and COLT storage.
-  float load = o.load_factor > 0.f ? o.load_factor : 0.5f;
+  float load = o.load_factor > 0.f ? o.load_factor : 0.25f;
   if (load > 0.9f) load = 0.9f;
   P->host_atoms.assign(na, AtomDev{});
   for (int a = 0; a < na; ++a) {
@@ -906,7 +905,10 @@ static void ensure_output(fj_prepared* P, uint64_t rows) {
 static void reset_state(fj_prepared* P, bool atoms) {
   fj_ctx* c = P->ctx;
   int na = int(P->q.atom_vars.size());
-  k_reset<<<na, 32, 0, c->stream>>>(P->d_atoms, na, c->d_res, atoms ? 1 : 0);
+  k_reset<<<std::max(na, 1), 32, 0, c->stream>>>(
+      P->d_atoms, na, c->d_res, atoms ? 1 : 0,
+      reinterpret_cast<unsigned int*>(P->roots_state),
+      P->roots_state ? int(sizeof(RootsState) / sizeof(unsigned int)) : 0);
   CK_LAUNCH("reset");
   P->kernels += 1;
 }

@@ -882,8 +882,13 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
 }
 
 // Reset the COLT state of every atom (nothing built) and/or the result.
-__global__ void k_reset(AtomDev* atoms, int n_atoms, ResultDev* res, int do_atoms) {
+__global__ void k_reset(AtomDev* atoms, int n_atoms, ResultDev* res, int do_atoms,
+                        unsigned int* zero, int n_zero) {
   int a = blockIdx.x;
+  // Words that must start at zero (the root-build barrier and counters,
+  // which leave themselves at zero only after a complete launch).
+  if (a == 0 && zero)
+    for (int i = threadIdx.x; i < n_zero; i += blockDim.x) zero[i] = 0;
   if (do_atoms && a < n_atoms && threadIdx.x == 0) {
     AtomDev& A = atoms[a];
     A.root_mat = 0;

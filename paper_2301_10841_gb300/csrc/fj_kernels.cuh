@@ -709,21 +709,20 @@ __global__ void k_force_reset_req(ForceJobs fj) {
 // resident (cudaLaunchCooperativeKernel), separated by grid barriers:
 //   A  compact the rows that pass the selection,
 //   B  size and clear each table and filter,
-//   C  insert the keys, count rows per key, list the new keys,
-//   D  give each new key its entry and its range of offsets,
+//   C  insert the keys and count rows per key,
+//   D  make each occupied slot an entry with its range of offsets,
 //   E  scatter the offsets,
 //   F  reset the fill cursors and record the level as forced.
 // Each pass splits the work of all jobs into one contiguous range per block
 // and takes several independent elements per thread at a time (the passes
-// are chains of dependent L2 accesses); offsets come from one counter per
-// job, advanced once per block and job in A, once per 2048 elements in C
-// and D.  Every barrier wait is bounded: on expiry the kernel sets
+// are chains of dependent L2 accesses); offsets come from counters per job,
+// advanced once per sweep of 8192 rows in A and of 2048 slots in D.  Every barrier wait is bounded: on expiry the kernel sets
 // kStTimeout and its blocks return; the host reports FJ_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
 
 constexpr int kRootThreads = 512;
 
-struct RootsState {        // zeroed before each launch
+struct RootsState {        // zero before each launch, and after each complete one
   unsigned int bar_count;  // blocks arrived at the current barrier
   unsigned int bar_gen;    // barriers completed
   unsigned int n_pass[FJ_MAX_ATOMS];
@@ -892,7 +891,8 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   __shared__ uint32_t s_mask[FJ_MAX_ATOMS], s_fon[FJ_MAX_ATOMS];
   __shared__ uint32_t s_np[FJ_MAX_ATOMS], s_nn[FJ_MAX_ATOMS];  // rows passing, new keys
   __shared__ uint32_t s_scan[33];
-  __shared__ uint32_t s_base;
+  __shared__ unsigned long long s_scan64[33];
+  __shared__ uint32_t s_base, s_base2;
   if (tid < uint32_t(nj)) {
     const int2 jb = fj.jobs[tid];
     const AtomDev& a = fj.atoms[jb.x];
@@ -1006,8 +1006,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   if (!grid_sync(cs, &res->status)) return;
 
   // C: insert every passing row's key (E per thread, their first
-  // compare-and-swaps in flight together) and count rows per key; list the
-  // new keys (their position in the list is their index under the root).
+  // compare-and-swaps in flight together) and count rows per key.
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
   block_range(s_off[nj], lo, hi);
   for (int j = 0; j < nj; ++j) {
@@ -1018,7 +1017,6 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     for (uint32_t r = a0 - s_off[j]; r < a1 - s_off[j]; r += E * NT) {
       const uint32_t r1 = a1 - s_off[j];
       uint32_t slot[E];
-      uint32_t claimed = 0;
       if (!J.wide) {
         uint64_t kw[E];
         uint32_t h[E];
@@ -1057,7 +1055,6 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
             const uint32_t fh = filter_hash(kw[u]);
             atomicOr(&J.filter[fh & (J.filter_words - 1)], bloom_bits(fh));
           }
-          if (cl) claimed |= 1u << u;
         }
       } else {
 #pragma unroll
@@ -1071,7 +1068,6 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
                                 J.nk > 2 ? uint32_t(__ldg(J.kc[2] + row)) : 0u);
           bool cl = false;
           slot[u] = ht_insert_wide(J.ht, mask, kw, cl, &res->status);
-          if (cl) claimed |= 1u << u;
         }
       }
 #pragma unroll
@@ -1081,68 +1077,61 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
         if (slot[u] != kNone) atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u);
         J.tmp_slot[i] = slot[u];
       }
-      uint32_t tot;
-      uint32_t pos = block_excl_scan<uint32_t>(__popc(claimed), s_scan, &tot);
-      if (tid == 0) s_base = tot ? atomicAdd(&cs->n_new[j], tot) : 0u;
-      __syncthreads();
-      pos += s_base;
-#pragma unroll
-      for (int u = 0; u < E; ++u) {
-        if (!(claimed >> u & 1u)) continue;
-        J.newslots[pos] = slot[u];
-        *slot_e(J.ht, J.wide, slot[u]) = pos;
-        ++pos;
-      }
     }
   }
   if (!grid_sync(cs, &res->status)) return;
-  if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[tid];
-  __syncthreads();
 
-  // D: entries of the new keys, each with its range inside the root's range
-  // (one advance of the root's fill cursor per E * blockDim keys).
-  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_nn[j] : 0u; });
+  // D: the occupied slots of each table (a slot is occupied once a row has
+  // been counted in it) become the root's entries, in slot order, each with
+  // its range of offsets inside the root's range: per sweep of the block's
+  // part of a table, one advance of the entry counter and one of the
+  // root's fill cursor.
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_mask[j] + 2 : 0u; });
   block_range(s_off[nj], lo, hi);
   for (int j = 0; j < nj; ++j) {
     const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
     if (a0 >= a1) continue;
     const RootJob& J = s_job[j];
-    for (uint32_t r = a0 - s_off[j]; r < a1 - s_off[j]; r += E * NT) {
-      const uint32_t r1 = a1 - s_off[j];
-      uint32_t s[E], cnt[E], sum = 0;
+    const uint32_t r1 = a1 - s_off[j];
+    for (uint32_t r = a0 - s_off[j]; r < r1; r += E * NT) {
+      uint32_t cnt[E], occ = 0, n_occ = 0, sum = 0;
       uint64_t kw[E];
 #pragma unroll
       for (int u = 0; u < E; ++u) {
-        const uint32_t i = r + u * NT + tid;
-        s[u] = i < r1 ? J.newslots[i] : 0u;
-      }
-#pragma unroll
-      for (int u = 0; u < E; ++u) {
-        const uint32_t i = r + u * NT + tid;
+        const uint32_t sl_i = r + u * NT + tid;
         cnt[u] = 0;
         kw[u] = 0;
-        if (i >= r1) continue;
+        if (sl_i >= r1) continue;
         if (J.wide) {
+          cnt[u] = J.ht[2 * size_t(sl_i) + 1].y;
           kw[u] = 0;  // wide entries keep only the parent (the root: 0)
-          cnt[u] = J.ht[2 * size_t(s[u]) + 1].y;
         } else {
-          const uint4 sl = J.ht[s[u]];
-          kw[u] = s[u] == s_mask[j] + 1 ? kEmptyKey : ((uint64_t(sl.y) << 32) | sl.x);
+          const uint4 sl = J.ht[sl_i];
           cnt[u] = sl.w;
+          kw[u] = sl_i == s_mask[j] + 1 ? kEmptyKey : ((uint64_t(sl.y) << 32) | sl.x);
         }
-        sum += cnt[u];
+        if (cnt[u]) {
+          occ |= 1u << u;
+          ++n_occ;
+          sum += cnt[u];
+        }
       }
-      uint32_t tot;
-      uint32_t b = block_excl_scan<uint32_t>(sum, s_scan, &tot);
-      if (tid == 0) s_base = tot ? atomicAdd(J.pfill, tot) : 0u;
+      unsigned long long tot;
+      const unsigned long long pre = block_excl_scan<unsigned long long>(
+          (static_cast<unsigned long long>(n_occ) << 32) | sum, s_scan64, &tot);
+      if (tid == 0) {
+        const uint32_t te = uint32_t(tot >> 32), tr = uint32_t(tot);
+        s_base = te ? atomicAdd(&cs->n_new[j], te) : 0u;
+        s_base2 = tr ? atomicAdd(J.pfill, tr) : 0u;
+      }
       __syncthreads();
-      b += s_base;  // the root's range starts at 0 (identity) or is all of perm
+      uint32_t e = J.base_e + s_base + uint32_t(pre >> 32);
+      uint32_t b = s_base2 + uint32_t(pre);  // the root's range starts at 0
 #pragma unroll
       for (int u = 0; u < E; ++u) {
-        const uint32_t i = r + u * NT + tid;
-        if (i >= r1) continue;
-        const uint32_t e = J.base_e + i;
-        *slot_e(J.ht, J.wide, s[u]) = e;
+        if (!(occ >> u & 1u)) continue;
+        const uint32_t sl_i = r + u * NT + tid;
+        *slot_e(J.ht, J.wide, sl_i) = e;
         J.key[e] = kw[u];
         J.count[e] = cnt[u];
         J.begin[e] = b;
@@ -1150,15 +1139,20 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
         if (J.cstate) J.cstate[e] = kUnforced;
         if (J.cnkeys) J.cnkeys[e] = 0;
         if (J.cfirst) J.cfirst[e] = 0;
+        ++e;
         b += cnt[u];
       }
+      __syncthreads();
     }
   }
   if (!grid_sync(cs, &res->status)) return;
+  if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[tid];
+  __syncthreads();
 
   // E: every passing row to its entry's range.
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
-  for (uint32_t x0 = blockIdx.x * E * NT; x0 < s_off[nj]; x0 += gridDim.x * E * NT) {
+  block_range(s_off[nj], lo, hi);
+  for (uint32_t x0 = lo; x0 < hi; x0 += E * NT) {
     uint32_t t[E], e[E];
     int jj[E];
 #pragma unroll
@@ -1166,7 +1160,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       const uint32_t x = x0 + u * NT + tid;
       t[u] = kNone;
       jj[u] = 0;
-      if (x >= s_off[nj]) continue;
+      if (x >= hi) continue;
       jj[u] = job_at(s_off, nj, x);
       t[u] = s_job[jj[u]].tmp_slot[x - s_off[jj[u]]];
     }
@@ -1222,6 +1216,10 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     L.cleared = 1;
     L.n_req = 0;
     L.n_in = 0;
+    // Every block read the counters before the last barrier: zero them for
+    // the next launch (the barrier words are back at zero already).
+    cs->n_pass[j] = 0;
+    cs->n_new[j] = 0;
   }
 }
 
