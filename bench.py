@@ -123,8 +123,7 @@ def probe_phase_bytes(fact, dims, theta):
     rows; k_i only for rows that survived the probes of D1..D(i-1)), 16 bytes
     per distinct dimension key probed (one hash slot each), and the 4-byte
     per-survivor reads of the tail (vector length, offset and attribute).
-    Computed from the data by a host pass; the same model is stated in
-    DESIGN.md."""
+    Computed from the data by a host pass."""
     n = len(fact["cols"][0])
     alive = np.ones(n, dtype=bool)
     total = 0
@@ -161,17 +160,17 @@ def measured_peaks():
 
 
 def profiled_traffic(kernel_hash):
-    """DRAM bytes per launch of the dominant kernels from the committed ncu
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
     import re
-    path = os.path.join(ROOT, "profiles", "scan_pipeline_star_F10M.md")
+    path = os.path.join(ROOT, "profiles", "scan_fused_star_F10M.md")
     try:
         with open(path) as f:
             text = f.read()
     except OSError:
         return None
     src = re.search(r"kernel_source:\s*([0-9a-f]+)", text)
-    tr = re.search(r"traffic_bytes_per_step:\s*([0-9]+)", text)
+    tr = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
     if src and tr and src.group(1) == kernel_hash:
         return int(tr.group(1))
     return None
@@ -348,7 +347,7 @@ def run_fj(args, rank, world):
     launch_s = expand_ns / max(1, expand_n) / 1e9
     achieved = alg / launch_s / 1e9 if launch_s > 0 else None
     khash = source_hash()
-    roofline = {"bound": "hbm", "kernel": "node-0 scan pipeline (k_scan_first + k_scan_rest)",
+    roofline = {"bound": "hbm", "kernel": "k_scan_fused (node 0: cover stream, all probes, aggregate)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
                 "traffic": profiled_traffic(khash), "algorithmic_bytes": alg,

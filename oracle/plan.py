@@ -5,7 +5,7 @@ A plan is a list of nodes; a node is a list of subatoms; a subatom is a pair
 designated cover (Section 3.2, the convention after Def. 3.7).  Atoms are the
 query's atoms, given as their variable lists (``atom_vars[i]``).
 
-Readings of passages the paper leaves open (each also listed in the design doc):
+Readings of passages the paper leaves open:
 
 * ``binary2fj`` (Fig. 9): the "available variables" used while building the
   current node are all variables bound so far, including those of the

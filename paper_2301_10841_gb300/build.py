@@ -1,8 +1,8 @@
 """Build libfj.so in-tree with nvcc for sm_103a (GB300).
 
-Usage: ``python -m paper_2301_10841_gb300.build`` (or ``build()``).  The two
+Usage: ``python -m paper_2301_10841_gb300.build`` (or ``build()``).  The
 translation units are compiled in parallel and linked with the static CUDA
-runtime, so the library only needs the driver at run time.
+runtime, so the library needs only the NVIDIA driver (libcuda) at run time.
 """
 
 from __future__ import annotations
