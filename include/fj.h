@@ -54,6 +54,7 @@ typedef int32_t fj_status;
 typedef struct fj_ctx fj_ctx;
 typedef struct fj_rel fj_rel;
 typedef struct fj_prepared fj_prepared;
+typedef struct fj_batch fj_batch;
 
 /* ------------------------------------------------------------------------ */
 /* Context                                                                   */
@@ -316,6 +317,33 @@ fj_status fj_execute_prepared_async(fj_prepared* prep);
 fj_status fj_prepared_result(fj_prepared* prep, fj_result* out);
 fj_status fj_reset_prepared(fj_prepared* prep);
 void fj_prepared_free(fj_prepared* prep);
+
+/* ------------------------------------------------------------------------ */
+/* Batches of independent queries (no counterpart in the paper)             */
+/* ------------------------------------------------------------------------ */
+
+/* A batch runs n prepared queries as one unit of work: every execution
+ * starts from scratch (COLT unbuilt, as after fj_reset_prepared), the queries
+ * run back to back on the context's stream, and the host synchronizes once
+ * for all n results.  Each query must be able to run without a host
+ * decision: COUNT or COUNT_MIN output, no FJ_FLAG_TIMING / EAGER flags, and
+ * node 0 as its only expanded node over a base-table cover (every factored
+ * binary2fj plan of a star, and of a chain of two relations); otherwise
+ * FJ_ERR_UNSUPPORTED names the first query that cannot.
+ *
+ * FJ_BATCH_GRAPH: fj_batch_create captures the launches of the whole batch
+ * once into a CUDA graph (the context's stream must not be capturing
+ * already); each fj_batch_execute is then one graph launch.  Without it, each
+ * execution enqueues the launches again.
+ *
+ * The batch borrows the prepared queries: they must outlive it and must not
+ * run on their own while a batch execution is in flight.  `results` holds n
+ * fj_result, filled as fj_prepared_result would fill them. */
+#define FJ_BATCH_GRAPH 1
+fj_status fj_batch_create(fj_ctx* ctx, int n, fj_prepared* const* preps, int flags,
+                          fj_batch** out);
+fj_status fj_batch_execute(fj_batch* batch, fj_result* results);
+void fj_batch_free(fj_batch* batch);
 
 /* Copy a materialized result's rows (n_out x n_head int32) to `dst`, a
  * device pointer if dst_is_device != 0 else a host pointer.  Synchronizes the

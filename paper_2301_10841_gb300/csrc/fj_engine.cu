@@ -41,8 +41,6 @@ struct fj_ctx {
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;
   int n_sm = 0;
-  ResultDev* d_res = nullptr;
-  ResultDev* h_res = nullptr;   // pinned
   uint64_t* h_total = nullptr;  // pinned
   void* d_partials = nullptr;   // scan partials: kMaxScanJobs x kScanBlocks x 8 B
   std::set<fj_prepared*> preps;  // live prepared plans (released by destroy)
@@ -168,6 +166,8 @@ struct fj_prepared {
   bool scan0 = false;
   ScanDev sc0{};
   int fuse_blocks = 0;  // > 0: node 0 runs as one k_scan_fused launch of this many blocks
+  ResultDev* d_res = nullptr;  // this query's result block (device)
+  ResultDev* h_res = nullptr;  // and its pinned host copy
   RootsState* roots_state = nullptr;  // k_force_roots barrier
   int roots_grid = 0;                 // > 0: root-only forces run as one cooperative launch
   uint64_t kernels = 0;
@@ -227,7 +227,7 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
   cudaEvent_t t0 = P->timing() ? P->mark() : nullptr;
   if (roots && P->roots_grid > 0) {
     RootsState* cs = P->roots_state;  // zero: set by k_reset, left so by each launch
-    ResultDev* rd = c->d_res;
+    ResultDev* rd = P->d_res;
     void* args[] = {&fj, &cs, &rd};
     CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_force_roots),
                                    dim3(P->roots_grid), dim3(kRootThreads), args, 0, s));
@@ -244,13 +244,13 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
   CK_LAUNCH("force prepare");
   P->kernels += 3;
   if (!roots) run_scan<uint32_t>(P, RowOffOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
-  k_force_insert<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, c->d_res);
+  k_force_insert<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, P->d_res);
   CK_LAUNCH("force insert");
   P->kernels += 1;
   if (!roots) run_scan<uint32_t>(P, ChildFirstOp{P->d_atoms, d_jobs}, n_jobs, ub_req);
   k_force_assign<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
   k_force_scatter<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj);
-  k_force_finish<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, c->d_res);
+  k_force_finish<<<dim3(g_rows, n_jobs), kThreads, 0, s>>>(fj, P->d_res);
   k_force_reset_req<<<n_jobs, 32, 0, s>>>(fj);
   CK_LAUNCH("force finish");
   P->kernels += 4;
@@ -261,9 +261,9 @@ template <int R>
 void launch_expand_r(fj_prepared* P, int grid, const NodeDev& nd) {
   fj_ctx* c = P->ctx;
   if (nd.dynamic)
-    k_expand<R><<<grid, kThreads, P->smem_expand, c->stream>>>(nd, P->d_atoms, c->d_res);
+    k_expand<R><<<grid, kThreads, P->smem_expand, c->stream>>>(nd, P->d_atoms, P->d_res);
   else
-    k_expand_static<R><<<grid, kThreads, P->smem_expand, c->stream>>>(nd, P->d_atoms, c->d_res);
+    k_expand_static<R><<<grid, kThreads, P->smem_expand, c->stream>>>(nd, P->d_atoms, P->d_res);
 }
 
 template <int R>
@@ -300,7 +300,7 @@ void run_scan_chunk(fj_prepared* P, NodeDev& nd) {
   const ScanDev& sc = P->sc0;
   if (P->fuse_blocks > 0) {
     k_scan_fused<kFuseR><<<P->fuse_blocks, kThreads, kFuseSmem, s>>>(nd, sc, P->d_atoms,
-                                                                     c->d_res);
+                                                                     P->d_res);
     CK_LAUNCH("scan fused");
     P->kernels += 1;
     return;
@@ -308,14 +308,14 @@ void run_scan_chunk(fj_prepared* P, NodeDev& nd) {
   int cap_blocks = c->n_sm * 8;
   k_scan_reset<<<1, 32, 0, s>>>(sc);
   int g1 = blocks_for(nd.chunk_end - nd.chunk_begin, kScanR * kThreads, cap_blocks);
-  k_scan_first<kScanR><<<g1, kThreads, 0, s>>>(nd, sc, c->d_res);
+  k_scan_first<kScanR><<<g1, kThreads, 0, s>>>(nd, sc, P->d_res);
   CK_LAUNCH("scan first");
   P->kernels += 2;
   // Survivors are about a tenth of the rows in a selective join; size the
   // grid for a quarter of them, the loop strides over the rest.
   uint64_t est = std::max<uint64_t>(1, (nd.chunk_end - nd.chunk_begin) / 4);
   int g2 = blocks_for(est, 4 * kThreads, cap_blocks);
-  k_scan_rest<4><<<g2, kThreads, 0, s>>>(nd, sc, P->d_atoms, c->d_res);
+  k_scan_rest<4><<<g2, kThreads, 0, s>>>(nd, sc, P->d_atoms, P->d_res);
   CK_LAUNCH("scan rest");
   P->kernels += 1;
 }
@@ -906,7 +906,7 @@ static void reset_state(fj_prepared* P, bool atoms) {
   fj_ctx* c = P->ctx;
   int na = int(P->q.atom_vars.size());
   k_reset<<<std::max(na, 1), 32, 0, c->stream>>>(
-      P->d_atoms, na, c->d_res, atoms ? 1 : 0,
+      P->d_atoms, na, P->d_res, atoms ? 1 : 0,
       reinterpret_cast<unsigned int*>(P->roots_state),
       P->roots_state ? int(sizeof(RootsState) / sizeof(unsigned int)) : 0);
   CK_LAUNCH("reset");
@@ -949,11 +949,18 @@ static uint64_t elapsed_ns(cudaEvent_t a, cudaEvent_t b) {
   return uint64_t(double(ms) * 1e6);
 }
 
+static void interpret_result(fj_prepared* P, fj_result* out, bool* retry);
+
 static void read_result(fj_prepared* P, fj_result* out, bool* retry) {
   fj_ctx* c = P->ctx;
-  CK(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(P->h_res, P->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  const ResultDev& r = *c->h_res;
+  interpret_result(P, out, retry);
+}
+
+// The result of the last execution from its host copy (already fetched).
+static void interpret_result(fj_prepared* P, fj_result* out, bool* retry) {
+  const ResultDev& r = *P->h_res;
   *retry = false;
   if (r.status & kStTableFull) fail(FJ_ERR_CUDA, "internal: COLT hash level overfilled");
   if (r.status & kStItemsOverflow) fail(FJ_ERR_CUDA, "internal: partial-tuple buffer overflow");
@@ -1019,7 +1026,7 @@ static void execute(fj_prepared* P, fj_result* out) {
         fail(FJ_ERR_OUTPUT_OVERFLOW, "more output rows than list_limit");
       return;
     }
-    uint64_t need = P->ctx->h_res->n_out;
+    uint64_t need = P->h_res->n_out;
     if (P->opts.list_limit) need = std::min<uint64_t>(need, P->opts.list_limit);
     ensure_output(P, need);
   }
@@ -1048,6 +1055,7 @@ static void prepared_release(fj_prepared* P) {
   for (void* p : P->allocs) dfree(P->ctx, p);
   if (P->d_out) dfree(P->ctx, P->d_out);
   cudaStreamSynchronize(P->ctx->stream);
+  if (P->h_res) cudaFreeHost(P->h_res);
   delete P;
 }
 
@@ -1084,6 +1092,8 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
   }
   CK(cudaSetDevice(ctx->device));
   try {
+    P->d_res = P->alloc<ResultDev>(1);
+    CK(cudaMallocHost(&P->h_res, sizeof(ResultDev)));
     compile(P.get());
     upload_atoms(P.get(), query);
     finalize_nodes(P.get());
@@ -1092,10 +1102,135 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
     reset_state(P.get(), true);
   } catch (...) {
     for (void* p : P->allocs) dfree(ctx, p);
+    if (P->h_res) cudaFreeHost(P->h_res);
     throw;
   }
   ctx->preps.insert(P.get());
   return P.release();
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many prepared queries as one unit of work (no counterpart in the
+// paper).  Every query runs from scratch, back to back on the context's
+// stream, and the host synchronizes once for all results; with
+// FJ_BATCH_GRAPH the whole sequence is captured once into a CUDA graph and
+// each execution is one graph launch.
+// ---------------------------------------------------------------------------
+
+struct fj_batch {
+  fj_ctx* ctx = nullptr;
+  std::vector<fj_prepared*> preps;
+  int flags = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> kernels, chunks;  // per query, as enqueued
+};
+
+// A query can be batched when nothing in its execution waits for the host:
+// aggregate output, no timing or eager builds, and node 0 as its only
+// expanded node with a total known on the host (its cover is a base table).
+static bool batchable(const fj_prepared* P, std::string* why) {
+  if (P->materialize) {
+    *why = "materialized output (the output size is decided on the host)";
+    return false;
+  }
+  if (P->opts.flags & (FJ_FLAG_TIMING | FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT)) {
+    *why = "timing or eager-build flags";
+    return false;
+  }
+  const NodeDev& n0 = P->nd[0];
+  const SubDev& S0 = n0.sub[0];
+  bool host_known = P->scan0 || (!n0.dynamic && S0.last && S0.lvl == 0 && !P->explicit_built);
+  if (n0.mode == kModeItems || !host_known) {
+    *why = "a node after node 0 is expanded (its input size is read back by the host)";
+    return false;
+  }
+  return true;
+}
+
+static void batch_enqueue(fj_batch* B) {
+  for (size_t i = 0; i < B->preps.size(); ++i) {
+    fj_prepared* P = B->preps[i];
+    begin_execution(P);
+    reset_state(P, true);
+    run_once(P);
+    CK(cudaMemcpyAsync(P->h_res, P->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost,
+                       B->ctx->stream));
+    B->kernels[i] = P->kernels;
+    B->chunks[i] = P->chunks;
+  }
+}
+
+static fj_batch* batch_create(fj_ctx* ctx, int n, fj_prepared* const* preps, int flags) {
+  if (!ctx || n < 0 || (n > 0 && !preps)) fail(FJ_ERR_INVALID_ARG, "bad batch arguments");
+  std::unique_ptr<fj_batch> B(new fj_batch);
+  B->ctx = ctx;
+  B->flags = flags;
+  for (int i = 0; i < n; ++i) {
+    fj_prepared* P = preps[i];
+    if (!P || P->ctx != ctx) fail(FJ_ERR_INVALID_ARG, "query of another context in the batch");
+    std::string why;
+    if (!batchable(P, &why))
+      fail(FJ_ERR_UNSUPPORTED, "batch query " + std::to_string(i) + ": " + why);
+    B->preps.push_back(P);
+  }
+  B->kernels.assign(n, 0);
+  B->chunks.assign(n, 0);
+  if (flags & FJ_BATCH_GRAPH) {
+    // Capture on a private stream (the context's stream may be the legacy
+    // default stream, which cannot be captured); the graph is launched on
+    // the context's stream.
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = cap;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        batch_enqueue(B.get());
+      } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(cap, &g);
+        if (g) cudaGraphDestroy(g);
+        ctx->stream = saved;
+        cudaStreamDestroy(cap);
+        throw;
+      }
+      e = cudaStreamEndCapture(cap, &B->graph);
+    }
+    ctx->stream = saved;
+    cudaStreamDestroy(cap);
+    CK(e);
+    CK(cudaGraphInstantiate(&B->exec, B->graph, 0));
+  }
+  return B.release();
+}
+
+static void batch_execute(fj_batch* B, fj_result* results) {
+  fj_ctx* c = B->ctx;
+  CK(cudaSetDevice(c->device));
+  if (B->exec) {
+    CK(cudaGraphLaunch(B->exec, c->stream));
+  } else {
+    batch_enqueue(B);
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < B->preps.size(); ++i) {
+    fj_prepared* P = B->preps[i];
+    P->kernels = B->kernels[i];
+    P->chunks = B->chunks[i];
+    bool retry = false;
+    interpret_result(P, &results[i], &retry);
+  }
+}
+
+static void batch_free(fj_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  delete B;
 }
 
 // ---------------------------------------------------------------------------
@@ -1123,9 +1258,7 @@ fj_status fj_ctx_create(int device, void* cuda_stream, fj_ctx** out) {
     CK(cudaMemPoolCreate(&c->pool, &props));
     uint64_t keep = ~0ull;
     CK(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
-    CK(cudaMallocHost(&c->h_res, sizeof(ResultDev)));
     CK(cudaMallocHost(&c->h_total, sizeof(uint64_t)));
-    c->d_res = dalloc<ResultDev>(c, 1);
     c->d_partials = dalloc<uint64_t>(c, size_t(kMaxScanJobs) * kScanBlocks);
     CK(cudaStreamSynchronize(c->stream));
     *out = c;
@@ -1137,10 +1270,8 @@ void fj_ctx_destroy(fj_ctx* c) {
   cudaSetDevice(c->device);
   while (!c->preps.empty()) prepared_release(*c->preps.begin());
   while (!c->rels.empty()) fj_release_relation(c, *c->rels.begin());
-  dfree(c, c->d_res);
   dfree(c, c->d_partials);
   cudaStreamSynchronize(c->stream);
-  if (c->h_res) cudaFreeHost(c->h_res);
   if (c->h_total) cudaFreeHost(c->h_total);
   if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
@@ -1306,3 +1437,21 @@ void fj_result_free(fj_ctx* c, fj_result* res) {
 }
 
 }  // extern "C"
+
+extern "C" fj_status fj_batch_create(fj_ctx* ctx, int n, fj_prepared* const* preps, int flags,
+                                     fj_batch** out) {
+  return guarded([&] {
+    if (!out) fail(FJ_ERR_INVALID_ARG, "NULL output");
+    *out = batch_create(ctx, n, preps, flags);
+  });
+}
+
+extern "C" fj_status fj_batch_execute(fj_batch* batch, fj_result* results) {
+  return guarded([&] {
+    if (!batch || (!batch->preps.empty() && !results)) fail(FJ_ERR_INVALID_ARG, "NULL argument");
+    batch_execute(batch, results);
+  });
+}
+
+extern "C" void fj_batch_free(fj_batch* batch) { batch_free(batch); }
+

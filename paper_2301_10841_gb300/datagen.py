@@ -137,6 +137,81 @@ def star_query(fact, dim_rels, theta=STAR_THETA):
 
 
 # ---------------------------------------------------------------------------
+# Batches of independent PK-FK queries
+# ---------------------------------------------------------------------------
+
+BATCH_THETA = 500_000_000  # payload uniform in [0, 1e9): keeps 50% in expectation
+
+
+def _pk_relation(name, n, fk_targets, s, rng):
+    """n rows: a dense unique key 0..n-1 (when this relation is referenced),
+    one Zipf(s) foreign key per target size (ranks through a seeded
+    permutation), and two int32 payload columns uniform in [0, 1e9)."""
+    cols = [np.arange(n, dtype=np.int32)]
+    for nt in fk_targets:
+        perm = rng.permutation(nt)
+        cols.append(perm[zipf_ranks(nt, s, n, rng)].astype(np.int32))
+    for _ in range(2):
+        cols.append(rng.integers(0, 1_000_000_000, size=n, dtype=np.int64).astype(np.int32))
+    return {"name": name, "cols": cols}
+
+
+def batch_query(q, min_rows=1_000, max_rows=2_000_000, base_seed=4):
+    """Query q of the batched workload (seed base_seed + q): a chain or a star
+    (q even: chain) of 2..6 relations with row counts log-uniform in
+    [min_rows, max_rows]; every referenced relation has a dense unique key,
+    foreign keys are Zipf(s) with s uniform in [0.5, 1.5], and the second
+    payload column of every referenced relation carries the selection
+    p2 < 5e8.  Returns (atoms, left-deep order, MIN variables): the MIN of
+    the first payload column of every relation.
+
+    Chain R1 -> R2 -> ... -> Rk: R1(a1, p), Ri(a_{i-1}, a_i, p, p2),
+    Rk(a_{k-1}, p, p2).  Star F -> D1..D(k-1): F(a1..a(k-1), p),
+    Di(ai, p, p2).  Key columns not referenced are left out of the atoms."""
+    rng = _rng(base_seed + q)
+    k = int(rng.integers(2, 7))
+    s = float(rng.uniform(0.5, 1.5))
+    sizes = [int(round(np.exp(rng.uniform(np.log(min_rows), np.log(max_rows))))) for _ in range(k)]
+    atoms, mins = [], []
+    nv = 0
+
+    def fresh():
+        nonlocal nv
+        nv += 1
+        return nv - 1
+
+    if q % 2 == 0:  # chain
+        link = [fresh() for _ in range(k - 1)]
+        for i in range(k):
+            targets = [sizes[i + 1]] if i + 1 < k else []
+            rel = _pk_relation(f"Q{q}R{i + 1}", sizes[i], targets, s, rng)
+            p, p2 = fresh(), fresh()
+            mins.append(p)
+            if i == 0:  # key, fk, p, p2 -> R1(a1, p)
+                atoms.append(atom(rel, [link[0], p], rel_cols=[1, 2]))
+            elif i + 1 < k:  # key, fk, p, p2
+                atoms.append(atom(rel, [link[i - 1], link[i], p, p2], rel_cols=[0, 1, 2, 3],
+                                  preds=[(3, "<", BATCH_THETA)]))
+            else:  # key, p, p2
+                atoms.append(atom(rel, [link[i - 1], p, p2], rel_cols=[0, 1, 2],
+                                  preds=[(2, "<", BATCH_THETA)]))
+    else:  # star
+        link = [fresh() for _ in range(k - 1)]
+        fact = _pk_relation(f"Q{q}F", sizes[0], sizes[1:], s, rng)
+        p = fresh()
+        fresh()
+        mins.append(p)
+        atoms.append(atom(fact, link + [p], rel_cols=list(range(1, k)) + [k]))
+        for i in range(1, k):
+            rel = _pk_relation(f"Q{q}D{i}", sizes[i], [], s, rng)
+            p, p2 = fresh(), fresh()
+            mins.append(p)
+            atoms.append(atom(rel, [link[i - 1], p, p2], rel_cols=[0, 1, 2],
+                              preds=[(2, "<", BATCH_THETA)]))
+    return atoms, list(range(k)), mins
+
+
+# ---------------------------------------------------------------------------
 # Small random queries for property tests
 # ---------------------------------------------------------------------------
 

@@ -117,6 +117,9 @@ _sig = {
     "fj_execute_prepared_async": ([_vp], ctypes.c_int),
     "fj_prepared_result": ([_vp, _P(_Result)], ctypes.c_int),
     "fj_prepared_free": ([_vp], None),
+    "fj_batch_create": ([_vp, ctypes.c_int, _P(_vp), ctypes.c_int, _P(_vp)], ctypes.c_int),
+    "fj_batch_execute": ([_vp, _P(_Result)], ctypes.c_int),
+    "fj_batch_free": ([_vp], None),
     "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
     "fj_result_free": ([_vp, _P(_Result)], None),
     "fj_join2_count_noalloc": ([_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp],
@@ -285,10 +288,13 @@ class Context:
 
     def close(self):
         if self.handle:
-            # fj_ctx_destroy releases every relation and prepared plan.
+            # fj_ctx_destroy releases every relation and prepared plan;
+            # batches are freed here.
             for ref in self._children:
                 obj = ref()
                 if obj is not None:
+                    if isinstance(obj, Batch):
+                        obj.free()
                     obj.handle = _vp()
             self._children = []
             _lib.fj_ctx_destroy(self.handle)
@@ -399,6 +405,8 @@ class Prepared:
         self.ctx = ctx
         self.min_vars = list(min_vars or [])
         self.out_mode = out_mode
+        # The library borrows the relations' columns: keep them alive.
+        self._rels = [a["rel"] for a in atoms]
         q, p = _QueryC(atoms, head), _PlanC(plan)
         o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags)
         self.handle = _vp()
@@ -437,3 +445,35 @@ class Prepared:
             self.free()
         except Exception:
             pass
+
+
+class Batch:
+    """fj_batch_create / fj_batch_execute: prepared queries run back to back
+    from scratch with one synchronization; ``graph=True`` captures them once
+    into a CUDA graph (FJ_BATCH_GRAPH) so each execution is one launch."""
+
+    def __init__(self, ctx, preps, graph=False):
+        self.ctx = ctx
+        self.preps = list(preps)
+        arr = (_vp * max(1, len(self.preps)))(*[p.handle for p in self.preps])
+        self.handle = _vp()
+        _check(_lib.fj_batch_create(ctx.handle, len(self.preps), arr, 1 if graph else 0,
+                                    ctypes.byref(self.handle)))
+        ctx._adopt(self)
+
+    def execute(self):
+        res = (_Result * max(1, len(self.preps)))()
+        _check(_lib.fj_batch_execute(self.handle, res))
+        return [Result(res[i], None, p.min_vars) for i, p in enumerate(self.preps)]
+
+    def free(self):
+        if self.handle:
+            _lib.fj_batch_free(self.handle)
+        self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+

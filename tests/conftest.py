@@ -18,3 +18,12 @@ def fj():
     """The CUDA library binding (loads libfj.so; fails loudly if missing)."""
     from paper_2301_10841_gb300 import fj as fjmod
     return fjmod
+
+
+@pytest.fixture(scope="module")
+def ctx(fj):
+    """A context on cuda:0 for the tests of one module."""
+    c = fj.Context(0)
+    yield c
+    c.close()
+

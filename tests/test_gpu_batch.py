@@ -1,0 +1,78 @@
+"""Batches of independent PK-FK chain and star queries (fj_batch_*): every
+query's COUNT and MINs equal the oracle's hash join of the same query, run
+eagerly and as one captured CUDA graph (replayed twice), and a query that
+needs a host decision is refused with FJ_ERR_UNSUPPORTED."""
+
+import numpy as np
+import pytest
+
+import oracle
+from fjtest import device_atoms
+from paper_2301_10841_gb300 import datagen as G
+
+pytestmark = pytest.mark.gpu
+
+
+def _batchable(atoms, q):
+    # Stars, and chains of two relations, run node 0 alone.
+    return q % 2 == 1 or len(atoms) == 2
+
+
+def test_batch_matches_oracle(fj, ctx):
+    preps, want = [], []
+    for q in range(48):
+        atoms, order, mins = G.batch_query(q, max_rows=60_000)
+        if not _batchable(atoms, q):
+            continue
+        c, m, _ = oracle.binary_join(atoms, order=order, min_vars=mins)
+        want.append((c, m))
+        dev, _ = device_atoms(fj, ctx, atoms)
+        plan = fj.binary_to_free_plan(dev, order, factor=True)
+        preps.append(fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins))
+    assert len(preps) >= 20
+    for graph in (False, True):
+        b = fj.Batch(ctx, preps, graph=graph)
+        for _ in range(2):
+            got = [(r.count, r.mins) for r in b.execute()]
+            assert got == want
+        b.free()
+    # A prepared query still runs on its own after the batches.
+    r = preps[0].execute()
+    assert (r.count, r.mins) == want[0]
+
+
+def test_batch_refuses_host_decisions(fj, ctx):
+    atoms, order, mins = G.batch_query(0, max_rows=5_000)  # chain
+    assert len(atoms) > 2
+    dev, _ = device_atoms(fj, ctx, atoms)
+    plan = fj.binary_to_free_plan(dev, order, factor=True)
+    p = fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins)
+    with pytest.raises(fj.FJError) as ei:
+        fj.Batch(ctx, [p])
+    assert ei.value.status == -8 and "batch query 0" in str(ei.value)
+    m = fj.Prepared(ctx, dev, plan, out_mode="materialize")
+    with pytest.raises(fj.FJError):
+        fj.Batch(ctx, [m])
+
+
+def test_prepared_keeps_its_relations(fj, ctx):
+    """A prepared query borrows device columns: it must keep the relations
+    alive after the caller drops them (the allocator would reuse them)."""
+    import gc
+
+    import torch
+
+    def make():
+        atoms, order, mins = G.batch_query(1, max_rows=20_000)
+        dev, _ = device_atoms(fj, ctx, atoms)
+        plan = fj.binary_to_free_plan(dev, order, factor=True)
+        want = oracle.binary_join(atoms, order=order, min_vars=mins)[:2]
+        return fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins), want
+
+    p, want = make()
+    gc.collect()
+    junk = [torch.full((1 << 20,), 7, dtype=torch.int32, device="cuda") for _ in range(8)]
+    r = p.execute()
+    assert (r.count, r.mins) == want
+    del junk
+

@@ -16,13 +16,6 @@ from fjtest import device_atoms, gj_plan, plans_for, sort_rows
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx(fj):
-    c = fj.Context(0)
-    yield c
-    c.close()
-
-
 def _run_all_ways(fj, ctx, atoms, plan, min_vars, covers=("static", "fewest"), tiles=(256, 2048)):
     head = oracle.query_vars(atoms)
     want_c, want_m, want_t = oracle.binary_join(atoms, head=head, min_vars=min_vars,
