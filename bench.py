@@ -494,6 +494,150 @@ def run_rmat(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Third workload (--workload batched): 256 independent PK-FK chain and star
+# queries; the queries that run without a host decision form one batch
+# captured into a CUDA graph (one launch per execution), the others run one
+# by one; compared with all 256 run one by one with a synchronization each.
+# ---------------------------------------------------------------------------
+
+BATCH_METRIC = "tuples/sec (in+out), 256 batched PK-FK chain/star queries"
+
+
+def run_batched(args, rank, world):
+    import torch
+
+    from paper_2301_10841_gb300 import fj
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = fj.Context(local)
+    t_gen = time.perf_counter()
+    queries = []
+    in_tuples = 0
+    alg = 0  # compulsory bytes: every column of every atom read once
+    for q in range(args.n_queries):
+        atoms, order, mins = G.batch_query(q, max_rows=args.max_rows)
+        rels = {}
+        dq = []
+        for a in atoms:
+            key = id(a["rel"])
+            if key not in rels:
+                rels[key] = ctx.relation([torch.from_numpy(c).to(dev) for c in a["rel"]["cols"]])
+            dq.append({"rel": rels[key], "vars": a["vars"], "rel_cols": a["rel_cols"],
+                       "preds": a["preds"]})
+            in_tuples += len(a["cols"][0])
+            alg += sum(4 * len(c) for c in a["cols"])
+        plan = fj.binary_to_free_plan(dq, order, factor=True)
+        queries.append((dq, plan, mins))
+    t_gen = time.perf_counter() - t_gen
+    # Autotune each query (cover-batch size x load factor), untimed.
+    t_tune = time.perf_counter()
+    tuned, choice = [], []
+    for dq, plan, mins in queries:
+        p, cfg, _ = fj.autotune(ctx, dq, plan, out_mode="count_min", min_vars=mins,
+                                batch_sizes=(1024, 8192), load_factors=(0.25, 0.5), reps=1)
+        tuned.append(p)
+        choice.append(cfg)
+    t_tune = time.perf_counter() - t_tune
+    graphed, single = [], []
+    for i, p in enumerate(tuned):
+        try:
+            fj.Batch(ctx, [p]).free()
+            graphed.append(i)
+        except fj.FJError:
+            single.append(i)
+    batch = fj.Batch(ctx, [tuned[i] for i in graphed], graph=True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step_batched():
+        res = dict(zip(graphed, batch.execute()))
+        for i in single:
+            tuned[i].reset()
+            res[i] = tuned[i].execute()
+        return [(res[i].count, res[i].mins) for i in range(len(tuned))]
+
+    def step_plain():
+        out = []
+        for p in tuned:
+            p.reset()
+            r = p.execute()
+            out.append((r.count, r.mins))
+        return out
+
+    for _ in range(args.warmup):
+        expect = step_batched()
+        if step_plain() != expect:
+            raise SystemExit("plain and batched results differ")
+    out_tuples = sum(c for c, _ in expect)
+    launches = sum(r.counters["kernels"] for r in batch.execute())
+    for i in single:
+        tuned[i].reset()
+        launches += tuned[i].execute().counters["kernels"]
+
+    def timed(step):
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            got = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if got != expect:
+                raise SystemExit("result changed between steps")
+            times.append(e0.elapsed_time(e1))
+        return sum(times) / len(times)
+
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = timed(step_batched)
+    clk = clocks.stop()
+    ms_plain = timed(step_plain)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    per_rank = in_tuples + out_tuples
+    value = per_rank * world / (ms / 1000)
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (ms / 1000) / 1e9
+    line = {"metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.n_queries} PK-FK queries (datagen.batch_query, seeds "
+                                   f"4..{3 + args.n_queries}): chains and stars of 2-6 relations, "
+                                   f"rows log-uniform in [1e3, {args.max_rows:.0e}], Zipf FKs "
+                                   f"s in [0.5, 1.5], selection p2 < 5e8; COUNT + MIN(p1) each",
+                       "plan": "factor(binary2fj(order)) per query, autotuned cover-batch "
+                               "size and load factor",
+                       "graphed_queries": len(graphed), "single_queries": len(single),
+                       "l2": "flushed between steps (256 MB write)", "in_tuples": in_tuples},
+            "result": {"out_tuples": out_tuples},
+            "plain": {"ms_per_step": ms_plain,
+                      "value": per_rank * world / (ms_plain / 1000),
+                      "note": "every query reset and executed one by one, one sync each"},
+            "autotune": {"seconds": t_tune, "choices": {f"{b}/{l}": choice.count((b, l))
+                                                        for b, l in sorted(set(choice))}},
+            "generate_seconds": t_gen,
+            "roofline": {"bound": "hbm", "kernel": "whole batch (every launch)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "algorithmic_bytes": alg, "launch_us": ms * 1000},
+            "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": launches * args.steps, "impl": "fj"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -504,7 +648,9 @@ def main():
     ap.add_argument("--n-fact", type=int, default=N_FACT)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="star", choices=["star", "rmat-triangle"])
+    ap.add_argument("--workload", default="star", choices=["star", "rmat-triangle", "batched"])
+    ap.add_argument("--n-queries", type=int, default=256)
+    ap.add_argument("--max-rows", type=int, default=2_000_000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -521,6 +667,8 @@ def main():
             run_reference(args, rank, world)
         elif args.workload == "rmat-triangle":
             run_rmat(args, rank, world)
+        elif args.workload == "batched":
+            run_batched(args, rank, world)
         else:
             run_fj(args, rank, world)
     finally:

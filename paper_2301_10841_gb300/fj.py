@@ -477,3 +477,36 @@ class Batch:
         except Exception:
             pass
 
+
+def autotune(ctx, atoms, plan, out_mode="count", min_vars=None, cover="static",
+             batch_sizes=(256, 1024, 4096, 8192), load_factors=(0.25, 0.5), reps=2):
+    """Pick the cover-batch size and hash-level load factor with the shortest
+    execution (device time between CUDA events, best of ``reps`` runs from
+    scratch) and return ``(prepared, (batch_size, load_factor), ms)``; the
+    other candidates are freed.  Results do not depend on the choice."""
+    import torch
+    best = None
+    stream = torch.cuda.current_stream()
+    for bs in batch_sizes:
+        for lf in load_factors:
+            p = Prepared(ctx, atoms, plan, out_mode=out_mode, min_vars=min_vars,
+                         batch_size=bs, load_factor=lf, cover=cover)
+            t = None
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                p.reset()
+                e0.record(stream)
+                p.execute_async()
+                e1.record(stream)
+                p.result()
+                ms = e0.elapsed_time(e1)
+                t = ms if t is None else min(t, ms)
+            if best is None or t < best[2]:
+                if best is not None:
+                    best[0].free()
+                best = (p, (bs, lf), t)
+            else:
+                p.free()
+    return best
+
