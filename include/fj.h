@@ -55,6 +55,7 @@ typedef struct fj_ctx fj_ctx;
 typedef struct fj_rel fj_rel;
 typedef struct fj_prepared fj_prepared;
 typedef struct fj_batch fj_batch;
+typedef struct fj_model fj_model;
 
 /* ------------------------------------------------------------------------ */
 /* Context                                                                   */
@@ -353,6 +354,39 @@ fj_status fj_result_copy_tuples(fj_ctx* ctx, const fj_result* res, void* dst,
 
 /* Release the device buffer of a result (safe to call twice). */
 void fj_result_free(fj_ctx* ctx, fj_result* res);
+
+/* ------------------------------------------------------------------------ */
+/* The chooser's network (no counterpart in the paper)                       */
+/* ------------------------------------------------------------------------ */
+
+/* A three-layer perceptron y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with
+ * float32 parameters, trained by plain gradient descent on the mean squared
+ * error; the plan chooser uses it to predict the work of a candidate plan
+ * from sampled degree histograms.  Its forward, backward and update kernels
+ * run on the context's stream.  Parameters form one array: W1 (h1 x in_dim,
+ * row-major), b1 (h1), W2 (h2 x h1), b2 (h2), W3 (1 x h2), b3 (1); they start
+ * at zero and are set by the caller (fj_model_set_params).  Inputs are
+ * device pointers to n x in_dim row-major float32 rows (n <= max_batch, else
+ * FJ_ERR_INVALID_ARG); targets and outputs are n float32 on the device.
+ * Errors: FJ_ERR_INVALID_ARG, FJ_ERR_OOM, FJ_ERR_CUDA, with the reason in
+ * fj_model_last_error(). */
+fj_status fj_model_create(fj_ctx* ctx, int in_dim, int h1, int h2, int max_batch,
+                          fj_model** out);
+size_t fj_model_n_params(const fj_model* model);
+fj_status fj_model_set_params(fj_model* model, const float* host, size_t n);
+fj_status fj_model_get_params(fj_model* model, float* host, size_t n);
+/* Predictions for n rows into d_y (enqueued, not waited for). */
+fj_status fj_model_forward(fj_model* model, const float* d_x, int n, float* d_y);
+/* Gradient of the mean squared error (host, in the parameter layout) and
+ * the loss, without changing the parameters.  Synchronizes. */
+fj_status fj_model_gradients(fj_model* model, const float* d_x, const float* d_t, int n,
+                             float* host_grads, float* host_loss);
+/* One descent step: parameters -= lr * gradient; *host_loss (if not NULL)
+ * receives the loss before the step (then synchronizes). */
+fj_status fj_model_train_step(fj_model* model, const float* d_x, const float* d_t, int n,
+                              float lr, float* host_loss);
+const char* fj_model_last_error(void);
+void fj_model_free(fj_model* model);
 
 /* ------------------------------------------------------------------------ */
 /* Join without allocation (no counterpart in the paper)                     */

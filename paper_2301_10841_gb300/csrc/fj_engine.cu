@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "fj_ctx_access.h"
 #include "fj_scan.cuh"
 #include "fj_plan.h"
 
@@ -1455,3 +1456,6 @@ extern "C" fj_status fj_batch_execute(fj_batch* batch, fj_result* results) {
 
 extern "C" void fj_batch_free(fj_batch* batch) { batch_free(batch); }
 
+
+cudaStream_t fj_internal_ctx_stream(const fj_ctx* c) { return c->stream; }
+int fj_internal_ctx_device(const fj_ctx* c) { return c->device; }

@@ -212,6 +212,38 @@ def batch_query(q, min_rows=1_000, max_rows=2_000_000, base_seed=4):
 
 
 # ---------------------------------------------------------------------------
+# Queries for the plan chooser: 5-relation snowflakes and 5-cycles with Zipf
+# keys over a domain as large as the relation
+# ---------------------------------------------------------------------------
+
+def _zipf_col(n, domain, s, rng):
+    perm = rng.permutation(domain)
+    return perm[zipf_ranks(domain, s, n, rng)].astype(np.int32)
+
+
+def chooser_query(q, min_rows=10_000, max_rows=50_000, base_seed=5, kind=None):
+    """Query q (seed base_seed + q) for the chooser: a snowflake C(a,b),
+    D1(a,c), D2(b,d), S1(c,e), S2(d,f) (q even) or a 5-cycle R1(a,b), R2(b,c),
+    R3(c,d), R4(d,e), R5(e,a) (q odd), each relation with row count
+    log-uniform in [min_rows, max_rows] and every column Zipf(s), s uniform
+    in [0.8, 1.6], over a key domain of the relation's row count (through a
+    seeded permutation).  Returns (atoms, kind)."""
+    rng = _rng(base_seed + q)
+    kind = kind or ("snowflake" if q % 2 == 0 else "cycle")
+    s = float(rng.uniform(0.8, 1.6))
+    if kind == "snowflake":
+        shape = [[0, 1], [0, 2], [1, 3], [2, 4], [3, 5]]
+    else:
+        shape = [[0, 1], [1, 2], [2, 3], [3, 4], [4, 0]]
+    atoms = []
+    for i, vs in enumerate(shape):
+        n = int(round(np.exp(rng.uniform(np.log(min_rows), np.log(max_rows)))))
+        rel = {"name": f"C{q}R{i}", "cols": [_zipf_col(n, n, s, rng) for _ in vs]}
+        atoms.append(atom(rel, vs))
+    return atoms, kind
+
+
+# ---------------------------------------------------------------------------
 # Small random queries for property tests
 # ---------------------------------------------------------------------------
 

@@ -120,6 +120,17 @@ _sig = {
     "fj_batch_create": ([_vp, ctypes.c_int, _P(_vp), ctypes.c_int, _P(_vp)], ctypes.c_int),
     "fj_batch_execute": ([_vp, _P(_Result)], ctypes.c_int),
     "fj_batch_free": ([_vp], None),
+    "fj_model_create": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(_vp)],
+                        ctypes.c_int),
+    "fj_model_n_params": ([_vp], ctypes.c_size_t),
+    "fj_model_set_params": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "fj_model_get_params": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "fj_model_forward": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "fj_model_gradients": ([_vp, _vp, _vp, ctypes.c_int, _vp, _P(ctypes.c_float)], ctypes.c_int),
+    "fj_model_train_step": ([_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _P(ctypes.c_float)],
+                            ctypes.c_int),
+    "fj_model_last_error": ([], ctypes.c_char_p),
+    "fj_model_free": ([_vp], None),
     "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
     "fj_result_free": ([_vp, _P(_Result)], None),
     "fj_join2_count_noalloc": ([_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp],
@@ -509,4 +520,67 @@ def autotune(ctx, atoms, plan, out_mode="count", min_vars=None, cover="static",
             else:
                 p.free()
     return best
+
+
+class Model:
+    """fj_model_*: the chooser's three-layer perceptron (float32) with its
+    CUDA forward, backward and descent kernels.  Inputs are float32 CUDA
+    tensors of shape (n, in_dim); targets (n,)."""
+
+    def __init__(self, ctx, in_dim, h1=128, h2=64, max_batch=8192):
+        self.ctx = ctx
+        self.shape = (int(in_dim), int(h1), int(h2))
+        self.handle = _vp()
+        st = _lib.fj_model_create(ctx.handle, int(in_dim), int(h1), int(h2), int(max_batch),
+                                  ctypes.byref(self.handle))
+        if st != 0:
+            raise FJError(st, _lib.fj_model_last_error().decode())
+        self.n_params = int(_lib.fj_model_n_params(self.handle))
+
+    def _check(self, st):
+        if st != 0:
+            raise FJError(st, _lib.fj_model_last_error().decode())
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        self._check(_lib.fj_model_set_params(self.handle, _vp(a.ctypes.data), a.size))
+
+    def params(self):
+        a = np.empty(self.n_params, dtype=np.float32)
+        self._check(_lib.fj_model_get_params(self.handle, _vp(a.ctypes.data), a.size))
+        return a
+
+    def forward(self, x):
+        import torch
+        x = x.contiguous()
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        self._check(_lib.fj_model_forward(self.handle, _vp(x.data_ptr()), x.shape[0],
+                                          _vp(y.data_ptr())))
+        return y
+
+    def gradients(self, x, t):
+        x, t = x.contiguous(), t.contiguous()
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(_lib.fj_model_gradients(self.handle, _vp(x.data_ptr()), _vp(t.data_ptr()),
+                                            x.shape[0], _vp(g.ctypes.data), ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train_step(self, x, t, lr):
+        x, t = x.contiguous(), t.contiguous()
+        loss = ctypes.c_float()
+        self._check(_lib.fj_model_train_step(self.handle, _vp(x.data_ptr()), _vp(t.data_ptr()),
+                                             x.shape[0], float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def free(self):
+        if self.handle and self.ctx.handle:
+            _lib.fj_model_free(self.handle)
+        self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 

@@ -1,0 +1,94 @@
+"""The learned plan chooser.
+
+* The network's CUDA forward, backward and descent kernels against the
+  float64 restatement in oracle/mlp.py (itself pinned by finite differences).
+* The chooser trained on work the exact engine reports for engine-generated
+  queries: on held-out queries its orders give exactly the results of the
+  declared order (the converted binary plan, its fallback) and less work.
+"""
+
+import numpy as np
+import pytest
+
+from fjtest import device_atoms
+from oracle import mlp
+from paper_2301_10841_gb300 import chooser as C
+from paper_2301_10841_gb300 import datagen as G
+
+pytestmark = pytest.mark.gpu
+
+
+def test_model_kernels_match_oracle(fj, ctx):
+    import torch
+    d, h1, h2, n = C.IN_DIM, 128, 64, 700
+    rng = np.random.default_rng(11)
+    theta = C.init_params(d, h1, h2, seed=3)
+    x = rng.normal(0, 1, (n, d)).astype(np.float32)
+    t = rng.normal(0, 1, n).astype(np.float32)
+    m = fj.Model(ctx, d, h1, h2, max_batch=1024)
+    assert m.n_params == mlp.n_params(d, h1, h2)
+    m.set_params(theta)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y = m.forward(xd).cpu().numpy()
+    want, _ = mlp.forward(theta.astype(np.float64), x, d, h1, h2)
+    np.testing.assert_allclose(y, want, rtol=1e-4, atol=1e-4)
+    g, loss = m.gradients(xd, td)
+    g_want = mlp.gradients(theta.astype(np.float64), x, t, d, h1, h2)
+    assert np.linalg.norm(g - g_want) <= 1e-4 * np.linalg.norm(g_want)
+    assert abs(loss - mlp.loss(theta.astype(np.float64), x, t, d, h1, h2)) <= 1e-4 * loss
+    # Twenty descent steps follow the float64 trajectory.
+    th = theta.astype(np.float64)
+    for _ in range(20):
+        l_gpu = m.train_step(xd, td, 0.01)
+        l_cpu, th = mlp.sgd_step(th, x, t, d, h1, h2, 0.01)
+        assert abs(l_gpu - l_cpu) <= 1e-3 * l_cpu
+    np.testing.assert_allclose(m.params(), th, rtol=1e-3, atol=1e-4)
+    with pytest.raises(fj.FJError):
+        m.forward(torch.zeros((1025, d), device="cuda"))
+    m.free()
+
+
+def _engine_samples(fj, ctx, queries):
+    """(features, log2 work, count) of every candidate order of each query."""
+    out = []
+    for atoms, _ in queries:
+        dev, _ = device_atoms(fj, ctx, atoms)
+        hists = C.atom_histograms(atoms)
+        orders = C.candidate_orders([a["vars"] for a in atoms])
+        rows = []
+        for o in orders:
+            r = fj.execute(ctx, dev, fj.binary_to_free_plan(dev, o, factor=True),
+                           out_mode="count")
+            rows.append((C.order_features(atoms, o, hists), np.log2(C.work(r) + 1.0), r.count))
+        out.append((atoms, dev, hists, orders, rows))
+    return out
+
+
+def test_chooser_gain(fj, ctx):
+    import torch
+    train_q = [G.chooser_query(q, 3_000, 20_000) for q in range(120)]
+    test_q = [G.chooser_query(q, 20_000, 80_000) for q in range(1000, 1016)]
+    train = _engine_samples(fj, ctx, train_q)
+    for *_, rows in train:  # every order of a query gives the same count
+        assert len({c for _, _, c in rows}) == 1
+    x = np.stack([f for *_, rows in train for f, _, _ in rows])
+    y = np.array([w for *_, rows in train for _, w, _ in rows], dtype=np.float32)
+    scaler = C.fit_scaler(x)
+    mu, sd = float(y.mean()), float(y.std() + 1e-6)
+    model = fj.Model(ctx, C.IN_DIM, 128, 64, max_batch=8192)
+    model.set_params(C.init_params(C.IN_DIM, 128, 64, seed=1))
+    losses = C.train(model, torch.from_numpy(C.standardize(x, scaler)).cuda(),
+                     torch.from_numpy((y - mu) / sd).cuda())
+    assert losses[-1] < 0.6 * losses[0]
+    tot_declared = tot_chosen = tot_best = 0.0
+    for atoms, dev, hists, orders, rows in _engine_samples(fj, ctx, test_q):
+        chosen = C.choose(model, atoms, orders, hists, scaler)
+        i = orders.index(chosen)
+        assert rows[i][2] == rows[0][2]          # bit-exact whatever it picks
+        tot_declared += rows[0][1]
+        tot_chosen += rows[i][1]
+        tot_best += min(w for _, w, _ in rows)
+    print(f"log2 work summed over held-out queries: declared {tot_declared:.1f}, "
+          f"chosen {tot_chosen:.1f}, best {tot_best:.1f}")
+    assert tot_chosen < tot_declared
+    model.free()
