@@ -326,16 +326,18 @@ void fj_prepared_free(fj_prepared* prep);
 /* A batch runs n prepared queries as one unit of work: every execution
  * starts from scratch (COLT unbuilt, as after fj_reset_prepared), the queries
  * run back to back on the context's stream, and the host synchronizes once
- * for all n results.  Each query must be able to run without a host
- * decision: COUNT or COUNT_MIN output, no FJ_FLAG_TIMING / EAGER flags, and
- * node 0 as its only expanded node over a base-table cover (every factored
- * binary2fj plan of a star, and of a chain of two relations); otherwise
- * FJ_ERR_UNSUPPORTED names the first query that cannot.
+ * for all n results.  Inside a batch no node's size is read back by the
+ * host: each expanded node runs as one chunk as large as the next node's
+ * input buffer, and a node whose input would not fit fails the execution
+ * with FJ_ERR_UNSUPPORTED (run that query on its own).  Queries must have
+ * COUNT or COUNT_MIN output and no FJ_FLAG_TIMING / EAGER flags
+ * (fj_batch_create returns FJ_ERR_UNSUPPORTED naming the first that does
+ * not).
  *
  * FJ_BATCH_GRAPH: fj_batch_create captures the launches of the whole batch
- * once into a CUDA graph (the context's stream must not be capturing
- * already); each fj_batch_execute is then one graph launch.  Without it, each
- * execution enqueues the launches again.
+ * once into a CUDA graph (on a private stream); each fj_batch_execute is then
+ * one graph launch on the context's stream.  Without it, each execution
+ * enqueues the launches again.
  *
  * The batch borrows the prepared queries: they must outlive it and must not
  * run on their own while a batch execution is in flight.  `results` holds n

@@ -167,6 +167,7 @@ struct fj_prepared {
   bool scan0 = false;
   ScanDev sc0{};
   int fuse_blocks = 0;  // > 0: node 0 runs as one k_scan_fused launch of this many blocks
+  bool device_totals = false;  // node totals stay on the device (batched runs)
   ResultDev* d_res = nullptr;  // this query's result block (device)
   ResultDev* h_res = nullptr;  // and its pinned host copy
   RootsState* roots_state = nullptr;  // k_force_roots barrier
@@ -354,6 +355,7 @@ void run_node(fj_prepared* P, int k, uint64_t ub_items) {
   bool host_known = use_scan || (k == 0 && !nd.dynamic && S0.last && S0.lvl == 0 &&
                                  !(P->opts.flags & (FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT)) &&
                                  !P->explicit_built);
+  bool device_total = false;  // the total stays on the device (batches)
   if (host_known) {
     // The single root tuple iterates the cover's base table directly.
     total = P->host_atoms[S0.atom].n_rows;
@@ -364,7 +366,16 @@ void run_node(fj_prepared* P, int k, uint64_t ub_items) {
     run_scan<uint64_t>(P,
                        FanScanOp{nd.fan, nd.scan, nd.total, nd.n_items, nd.single_item},
                        1, ub_items);
-    sync_read_total(P, nd.total, &total);
+    if (P->device_totals) {
+      // One chunk as large as the next node's input buffer (or unbounded
+      // for the last node); the kernel clamps to the device total and
+      // flags a total the chunk cannot hold.
+      device_total = true;
+      total = nd.mode == kModeItems ? uint64_t(P->items[k + 1].cap) : ~0ull >> 1;
+      nd.check_total = 1;
+    } else {
+      sync_read_total(P, nd.total, &total);
+    }
   }
   if (total == 0) return;
   bool items_mode = nd.mode == kModeItems;
@@ -378,7 +389,9 @@ void run_node(fj_prepared* P, int k, uint64_t ub_items) {
     if (use_scan) {
       run_scan_chunk(P, nd);
     } else {
-      int grid = blocks_for(nd.chunk_end - c0, nd.tile, c->n_sm * P->expand_blocks_per_sm);
+      int grid = device_total ? c->n_sm * P->expand_blocks_per_sm
+                              : blocks_for(nd.chunk_end - c0, nd.tile,
+                                           c->n_sm * P->expand_blocks_per_sm);
       launch_expand(P, grid, nd);
       CK_LAUNCH("expand");
       P->kernels += 1;
@@ -964,7 +977,9 @@ static void interpret_result(fj_prepared* P, fj_result* out, bool* retry) {
   const ResultDev& r = *P->h_res;
   *retry = false;
   if (r.status & kStTableFull) fail(FJ_ERR_CUDA, "internal: COLT hash level overfilled");
-  if (r.status & kStItemsOverflow) fail(FJ_ERR_CUDA, "internal: partial-tuple buffer overflow");
+  if (r.status & kStItemsOverflow)
+    fail(FJ_ERR_UNSUPPORTED, "more partial tuples than one chunk holds (in a batch, a node's "
+                             "input must fit its buffer: run the query on its own)");
   if (r.status & kStCountOverflow) fail(FJ_ERR_COUNT_OVERFLOW, "COUNT(*) exceeds 2^64 - 1");
   if (r.status & kStTimeout) fail(FJ_ERR_TIMEOUT, "a bounded device wait ran out");
   std::memset(out, 0, sizeof(*out));
@@ -1139,13 +1154,6 @@ static bool batchable(const fj_prepared* P, std::string* why) {
     *why = "timing or eager-build flags";
     return false;
   }
-  const NodeDev& n0 = P->nd[0];
-  const SubDev& S0 = n0.sub[0];
-  bool host_known = P->scan0 || (!n0.dynamic && S0.last && S0.lvl == 0 && !P->explicit_built);
-  if (n0.mode == kModeItems || !host_known) {
-    *why = "a node after node 0 is expanded (its input size is read back by the host)";
-    return false;
-  }
   return true;
 }
 
@@ -1154,7 +1162,14 @@ static void batch_enqueue(fj_batch* B) {
     fj_prepared* P = B->preps[i];
     begin_execution(P);
     reset_state(P, true);
-    run_once(P);
+    P->device_totals = true;
+    try {
+      run_once(P);
+    } catch (...) {
+      P->device_totals = false;
+      throw;
+    }
+    P->device_totals = false;
     CK(cudaMemcpyAsync(P->h_res, P->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost,
                        B->ctx->stream));
     B->kernels[i] = P->kernels;

@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
   uint32_t n_items = nd.single_item ? 1u : *nd.n_items;
   uint64_t end = nd.chunk_end;
   if (!nd.single_item) end = min(end, nd.scan[n_items]);
+  if (nd.check_total && !nd.single_item && blockIdx.x == 0 && tid == 0 &&
+      nd.scan[n_items] > nd.chunk_end)
+    atomicOr(&res->status, kStItemsOverflow);
   __syncthreads();
 
   for (uint64_t tile = blockIdx.x;; tile += gridDim.x) {
@@ -630,6 +633,9 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
   uint32_t n_items = nd.single_item ? 1u : *nd.n_items;
   uint64_t end = nd.chunk_end;
   if (!nd.single_item) end = min(end, nd.scan[n_items]);
+  if (nd.check_total && !nd.single_item && blockIdx.x == 0 && tid == 0 &&
+      nd.scan[n_items] > nd.chunk_end)
+    atomicOr(&res->status, kStItemsOverflow);
   const SubDev& C = nd.sub[0];
   const AtomDev& ca = atoms[C.atom];
   __syncthreads();

@@ -194,6 +194,8 @@ struct NodeDev {
   uint64_t* total;                        // scan[n] copy for the host
   uint64_t chunk_begin;
   uint64_t chunk_end;
+  int check_total;                        // the host did not read the node's total:
+                                          // a total above chunk_end is an overflow
   int mode;
   int track_mult;                         // some probe ends an atom at a leaf
   // kModeItems.
