@@ -172,6 +172,7 @@ struct fj_prepared {
   ResultDev* h_res = nullptr;  // and its pinned host copy
   RootsState* roots_state = nullptr;  // k_force_roots barrier
   int roots_grid = 0;                 // > 0: root-only forces run as one cooperative launch
+  int roots_set = 0;                  // counter set of the next k_force_roots launch
   uint64_t kernels = 0;
   uint64_t chunks = 0;
   bool explicit_built = false;  // levels built outside the join since reset
@@ -221,16 +222,19 @@ void run_scan(fj_prepared* P, Op op, int n_jobs, uint64_t ub_n) {
 // COLT forcing of a batch of (atom, level) jobs.  `roots` says every job is
 // a root level (its single parent needs no row-offset or child-first scan).
 void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uint32_t ub_req,
-           bool roots) {
+           bool roots, bool request_all = false) {
   if (n_jobs == 0) return;
   fj_ctx* c = P->ctx;
   cudaStream_t s = c->stream;
   ForceJobs fj{P->d_atoms, d_jobs, n_jobs};
   cudaEvent_t t0 = P->timing() ? P->mark() : nullptr;
   if (roots && P->roots_grid > 0) {
-    RootsState* cs = P->roots_state;  // zero: set by k_reset, left so by each launch
+    RootsState* cs = P->roots_state;  // zeroed by k_reset at the start of the execution
+    int set = P->roots_set;
+    P->roots_set ^= 1;
+    int all = request_all ? 1 : 0;
     ResultDev* rd = P->d_res;
-    void* args[] = {&fj, &cs, &rd};
+    void* args[] = {&fj, &cs, &set, &all, &rd};
     CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_force_roots),
                                    dim3(P->roots_grid), dim3(kRootThreads), args, 0, s));
     P->kernels += 1;
@@ -344,11 +348,18 @@ void run_node(fj_prepared* P, int k, uint64_t ub_items) {
   cudaStream_t s = c->stream;
   NodeDev nd = P->nd[k];
   int g_items = blocks_for(ub_items, kThreads, c->n_sm * 8);
-  k_choose<<<g_items, kThreads, 0, s>>>(nd, P->d_atoms);
-  CK_LAUNCH("choose");
-  P->kernels += 1;
+  // Node 0 over a base-table cover whose jobs are all roots: its single
+  // root tuple reaches every one of them, so the root build requests them
+  // itself and no choice kernel runs.
+  const bool roots_direct = k == 0 && P->scan0 && nd.single_item && !nd.dynamic &&
+                            P->roots_only[0] && P->roots_grid > 0 && !P->jobs[0].empty();
+  if (!roots_direct) {
+    k_choose<<<g_items, kThreads, 0, s>>>(nd, P->d_atoms);
+    CK_LAUNCH("choose");
+    P->kernels += 1;
+  }
   force(P, P->d_jobs[k], int(P->jobs[k].size()), P->max_rows_job[k], P->max_req_job[k],
-        P->roots_only[k]);
+        P->roots_only[k], roots_direct);
   uint64_t total = 0;
   const SubDev& S0 = nd.sub[0];
   bool use_scan = k == 0 && P->scan0;

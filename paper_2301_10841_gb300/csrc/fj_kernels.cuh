@@ -368,6 +368,14 @@ __global__ void __launch_bounds__(kThreads) k_force_count(ForceJobs fj) {
     L.base = L.n_entries;
     if (job_identity(a, jb.y)) L.n_rows = a.n_rows;
   }
+  // The requested parents' fill cursors start this force's bump allocation
+  // of their children's ranges (the root build leaves them past the end).
+  if (jb.y > 1) {
+    LevelDev& P = a.L[jb.y - 1];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n_req;
+         i += gridDim.x * blockDim.x)
+      P.fill[L.req[i]] = 0;
+  }
   if (L.cleared) return;
   if (!job_identity(a, jb.y)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) L.n_in = a.n_pass;
@@ -722,11 +730,13 @@ __global__ void k_force_reset_req(ForceJobs fj) {
 
 constexpr int kRootThreads = 512;
 
-struct RootsState {        // zero before each launch, and after each complete one
-  unsigned int bar_count;  // blocks arrived at the current barrier
+struct RootsState {        // zero at the start of each execution (k_reset)
+  unsigned int bar_count;  // blocks arrived at the current barrier (back to 0 after each)
   unsigned int bar_gen;    // barriers completed
-  unsigned int n_pass[FJ_MAX_ATOMS];
-  unsigned int n_new[FJ_MAX_ATOMS];
+  // Per job: rows passing, keys.  Launches alternate between the two sets;
+  // a launch zeroes the set the next launch uses.
+  unsigned int n_pass[2][FJ_MAX_ATOMS];
+  unsigned int n_new[2][FJ_MAX_ATOMS];
 };
 
 constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about a second)
@@ -881,6 +891,7 @@ __device__ __forceinline__ uint32_t ht_insert_from(uint4* ht, uint32_t mask, uin
 }
 
 __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, RootsState* cs,
+                                                                 int set, int request_all,
                                                                  ResultDev* res) {
   constexpr int E = 4;  // independent elements per thread in C, D and E
   constexpr uint32_t NT = kRootThreads;
@@ -907,7 +918,9 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     for (int k = 0; k < 3; ++k) J.kc[k] = a.cols[L.kcol[k]];
     J.wide = L.wide;
     J.ident = !a.root_mat;
-    J.act = L.n_req > 0 && !L.cleared;
+    // request_all: node 0 of a single root tuple reaches every root of its
+    // jobs (what k_choose would request); otherwise the requests decide.
+    J.act = (request_all || L.n_req > 0) && !L.cleared;
     J.src = a.root_mat ? a.n_pass : a.n_rows;
     J.base_e = L.n_entries;
     J.tmp_row = a.tmp_row;
@@ -929,6 +942,10 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       J.pop[p] = a.pred_op[p];
       J.pval[p] = a.pred_val[p];
     }
+  }
+  if (blockIdx.x == 0 && tid < uint32_t(FJ_MAX_ATOMS)) {
+    cs->n_pass[set ^ 1][tid] = 0;
+    cs->n_new[set ^ 1][tid] = 0;
   }
   uint32_t lo, hi;
 
@@ -952,7 +969,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       for (int k = 0; k < 16; ++k) key[k] = (k1 && (pass >> k & 1u)) ? __ldg(J.kc[0] + row[k]) : 0;
       uint32_t tot;
       uint32_t o = block_excl_scan<uint32_t>(__popc(pass), s_scan, &tot);
-      if (tid == 0) s_base = tot ? atomicAdd(&cs->n_pass[j], tot) : 0u;
+      if (tid == 0) s_base = tot ? atomicAdd(&cs->n_pass[set][j], tot) : 0u;
       __syncthreads();
       o += s_base;
 #pragma unroll
@@ -966,7 +983,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     }
   }
   if (!grid_sync(cs, &res->status)) return;
-  if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[tid];
+  if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[set][tid];
   __syncthreads();
 
   // B: size each table for its passing rows; clear table and filter.
@@ -1121,7 +1138,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
           (static_cast<unsigned long long>(n_occ) << 32) | sum, s_scan64, &tot);
       if (tid == 0) {
         const uint32_t te = uint32_t(tot >> 32), tr = uint32_t(tot);
-        s_base = te ? atomicAdd(&cs->n_new[j], te) : 0u;
+        s_base = te ? atomicAdd(&cs->n_new[set][j], te) : 0u;
         s_base2 = tr ? atomicAdd(J.pfill, tr) : 0u;
       }
       __syncthreads();
@@ -1146,8 +1163,48 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     }
   }
   if (!grid_sync(cs, &res->status)) return;
-  if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[tid];
+  if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[set][tid];
   __syncthreads();
+
+  // The level's bookkeeping (block 0, while the others scatter; nothing in
+  // the scatter reads it).  The entries' fill cursors stay where the
+  // scatter leaves them: forcing the next level resets the cursors of the
+  // parents it regroups.
+  if (blockIdx.x == 0 && tid < uint32_t(nj)) {
+    const int j = tid;
+    const RootJob& J = s_job[j];
+    AtomDev& a = fj.atoms[fj.jobs[j].x];
+    LevelDev& L = a.L[fj.jobs[j].y];
+    LevelDev& P = a.L[fj.jobs[j].y - 1];
+    if (!J.act) {  // nothing to build: the request list starts empty again
+      L.n_req = 0;
+      L.n_in = 0;
+    } else {
+      const uint32_t np = s_np[j], nn = s_nn[j];
+      if (request_all) P.child_state[0] = kForced;
+      for (uint32_t r = 0; r < L.n_req; ++r) P.child_state[L.req[r]] = kForced;
+      P.child_first[0] = J.base_e;
+      P.child_nkeys[0] = nn;
+      if (J.ident) {
+        a.n_pass = np;
+        a.root_mat = 1;
+        P.begin[0] = 0;
+        P.count[0] = np;
+      }
+      atomicAdd(&res->ctr[FJ_CTR_ROOTS_BUILT], 1ull);
+      atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
+               1ull << fj.jobs[j].x);
+      atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)np);
+      L.n_rows = J.src;
+      L.n_tmp = np;
+      L.n_new = nn;
+      L.base = J.base_e;
+      L.n_entries = J.base_e + nn;
+      L.cleared = 1;
+      L.n_req = 0;
+      L.n_in = 0;
+    }
+  }
 
   // E: every passing row to its entry's range.
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
@@ -1173,53 +1230,6 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       const RootJob& J = s_job[jj[u]];
       J.perm[atomicAdd(&J.fill[e[u]], 1u)] = J.tmp_row[x0 + u * NT + tid - s_off[jj[u]]];
     }
-  }
-  if (!grid_sync(cs, &res->status)) return;
-
-  // F: fill cursors back to zero (the next level's bump allocation), and
-  // the level's bookkeeping.
-  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_nn[j] : 0u; });
-  for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
-    const int j = job_at(s_off, nj, x);
-    s_job[j].fill[s_job[j].base_e + x - s_off[j]] = 0;
-  }
-  if (blockIdx.x == 0 && tid < uint32_t(nj)) {
-    const int j = tid;
-    const RootJob& J = s_job[j];
-    AtomDev& a = fj.atoms[fj.jobs[j].x];
-    LevelDev& L = a.L[fj.jobs[j].y];
-    LevelDev& P = a.L[fj.jobs[j].y - 1];
-    if (!J.act) {  // nothing to build: the request list starts empty again
-      L.n_req = 0;
-      L.n_in = 0;
-      return;
-    }
-    const uint32_t np = s_np[j], nn = s_nn[j];
-    for (uint32_t r = 0; r < L.n_req; ++r) P.child_state[L.req[r]] = kForced;
-    P.child_first[0] = J.base_e;
-    P.child_nkeys[0] = nn;
-    if (J.ident) {
-      a.n_pass = np;
-      a.root_mat = 1;
-      P.begin[0] = 0;
-      P.count[0] = np;
-    }
-    atomicAdd(&res->ctr[FJ_CTR_ROOTS_BUILT], 1ull);
-    atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
-             1ull << fj.jobs[j].x);
-    atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)np);
-    L.n_rows = J.src;
-    L.n_tmp = np;
-    L.n_new = nn;
-    L.base = J.base_e;
-    L.n_entries = J.base_e + nn;
-    L.cleared = 1;
-    L.n_req = 0;
-    L.n_in = 0;
-    // Every block read the counters before the last barrier: zero them for
-    // the next launch (the barrier words are back at zero already).
-    cs->n_pass[j] = 0;
-    cs->n_new[j] = 0;
   }
 }
 
