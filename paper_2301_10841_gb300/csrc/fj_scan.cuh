@@ -727,6 +727,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
   const uint32_t* filt = s_fon[0] ? P.filter : nullptr;
   const uint32_t fw1 = P.filter_words - 1;
   const bool keep_h = !P.last;
+  const int nk1 = sc.n_probe > 1 ? sc.probe[1].nk : 0;  // second probe's key columns
+  const int32_t* kc1a = sc.probe[1].kcol[0];
+  const int32_t* kc1b = sc.probe[1].kcol[1];
+  const int32_t* kc1c = sc.probe[1].kcol[2];
   unsigned long long c_probe = 0, c_hit = 0, my_count = 0, surv = 0;
   bool any = false, timed_out = false;
   uint32_t n_surv = 0;  // survivors in the warp's region (the same in every lane)
@@ -776,6 +780,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
           out.row[pos] = rbase + jj[u];
           if (keep_h) out.h[0][pos] = e;
           if (out.mult) out.mult[pos] = P.last ? cnt : 1u;
+          // The second probe gathers this row's key later: bring its sector
+          // into L2 now (no register waits on it).
+          const uint32_t row = rbase + jj[u];
+          if (nk1 > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(kc1a + row));
+          if (nk1 > 1) asm volatile("prefetch.global.L2 [%0];" ::"l"(kc1b + row));
+          if (nk1 > 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(kc1c + row));
         }
         n_surv += __popc(hm);
       }
