@@ -234,6 +234,12 @@ fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
 #define FJ_FLAG_TIMING 4u      /* record CUDA events around the library's
                                   kernels (on the context's stream) and report
                                   device times in the FJ_CTR_*_NS counters */
+#define FJ_FLAG_TEST_TIMEOUT 8u  /* test of the bounded waits: the root
+                                  build's first grid barrier waits for one
+                                  block more than the grid has, so every
+                                  block gives up after its spin limit (about
+                                  a second) and the execution fails with
+                                  FJ_ERR_TIMEOUT; the context stays usable */
 
 typedef struct {
   uint32_t batch_size;   /* cover tuples per vectorized batch (Fig. 13);

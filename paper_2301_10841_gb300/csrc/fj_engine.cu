@@ -233,10 +233,18 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
     int set = P->roots_set;
     P->roots_set ^= 1;
     int all = request_all ? 1 : 0;
+    int test_timeout = (P->opts.flags & FJ_FLAG_TEST_TIMEOUT) ? 1 : 0;
     ResultDev* rd = P->d_res;
-    void* args[] = {&fj, &cs, &set, &all, &rd};
+    void* args[] = {&fj, &cs, &set, &all, &test_timeout, &rd};
     CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_force_roots),
                                    dim3(P->roots_grid), dim3(kRootThreads), args, 0, s));
+    if (test_timeout) {
+      // The test of the bounded waits stops the execution here: nothing may
+      // run on the levels the build left unbuilt.
+      CK(cudaMemcpyAsync(P->h_res, P->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (P->h_res->status & kStTimeout) fail(FJ_ERR_TIMEOUT, "a bounded device wait ran out");
+    }
     P->kernels += 1;
     if (t0) P->t_build.emplace_back(t0, P->mark());
     return;

@@ -201,6 +201,8 @@ constexpr int expand_min_blocks(int r) { return r >= 8 ? 1 : (r == 4 ? 2 : 3); }
 template <int R>
 __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
     k_expand(const __grid_constant__ NodeDev nd, AtomDev* atoms, ResultDev* res) {
+  // A root build whose bounded wait ran out left its levels unbuilt.
+  if (__syncthreads_or(threadIdx.x == 0 && (res->status & kStTimeout))) return;
   extern __shared__ uint32_t s_newh[];  // [n_sub][T]: handles found by probes
   constexpr int T = R * kThreads;
   __shared__ uint64_t s_range[2];
@@ -610,6 +612,8 @@ __device__ __forceinline__ void list_append(bool keep, uint32_t i, uint16_t* lis
 template <int R>
 __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
     k_expand_static(const __grid_constant__ NodeDev nd, AtomDev* atoms, ResultDev* res) {
+  // A root build whose bounded wait ran out left its levels unbuilt.
+  if (__syncthreads_or(threadIdx.x == 0 && (res->status & kStTimeout))) return;
   constexpr int T = R * kThreads;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint64_t* s_mult = reinterpret_cast<uint64_t*>(smem_raw);

@@ -743,14 +743,17 @@ constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about
 
 // Grid-wide barrier among all blocks of a cooperative launch.  Returns false
 // (in every thread of the block) when the wait ran out.
-__device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status) {
+// `extra` blocks more than the grid are awaited (a test of the bounded
+// wait: with extra > 0 the barrier never completes).
+__device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status,
+                                          uint32_t extra = 0) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = &cs->bar_gen;
     const unsigned int gen = *vgen;
     __threadfence();
-    if (atomicAdd(&cs->bar_count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&cs->bar_count, 1u) == gridDim.x + extra - 1) {
       cs->bar_count = 0;
       __threadfence();
       atomicAdd(&cs->bar_gen, 1u);
@@ -892,6 +895,7 @@ __device__ __forceinline__ uint32_t ht_insert_from(uint4* ht, uint32_t mask, uin
 
 __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, RootsState* cs,
                                                                  int set, int request_all,
+                                                                 int test_timeout,
                                                                  ResultDev* res) {
   constexpr int E = 4;  // independent elements per thread in C, D and E
   constexpr uint32_t NT = kRootThreads;
@@ -982,7 +986,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       __syncthreads();
     }
   }
-  if (!grid_sync(cs, &res->status)) return;
+  if (!grid_sync(cs, &res->status, test_timeout ? 1u : 0u)) return;
   if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[set][tid];
   __syncthreads();
 

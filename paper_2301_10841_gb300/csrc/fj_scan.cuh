@@ -178,6 +178,8 @@ template <int R>
 __global__ void __launch_bounds__(kThreads) k_scan_first(const __grid_constant__ NodeDev nd,
                                                          const __grid_constant__ ScanDev sc,
                                                          ResultDev* res) {
+  // A root build whose bounded wait ran out left its levels unbuilt.
+  if (__syncthreads_or(threadIdx.x == 0 && (res->status & kStTimeout))) return;
   static_assert(R % 4 == 0, "rows come in 16-byte groups");
   __shared__ uint32_t s_cnt, s_base;
   __shared__ uint32_t s_mask, s_fon;
@@ -509,6 +511,8 @@ template <int R>
 __global__ void __launch_bounds__(kThreads) k_scan_rest(const __grid_constant__ NodeDev nd,
                                                         const __grid_constant__ ScanDev sc,
                                                         AtomDev* atoms, ResultDev* res) {
+  // A root build whose bounded wait ran out left its levels unbuilt.
+  if (__syncthreads_or(threadIdx.x == 0 && (res->status & kStTimeout))) return;
   __shared__ uint32_t s_mask[FJ_MAX_SUB], s_fon[FJ_MAX_SUB];
   __shared__ int32_t s_min[FJ_MAX_VARS];
   __shared__ unsigned long long s_red[33];
@@ -675,6 +679,8 @@ template <int R>
 __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constant__ NodeDev nd,
                                                             const __grid_constant__ ScanDev sc,
                                                             AtomDev* atoms, ResultDev* res) {
+  // A root build whose bounded wait ran out left its levels unbuilt.
+  if (__syncthreads_or(threadIdx.x == 0 && (res->status & kStTimeout))) return;
   constexpr uint32_t T = kFuseTile, NS = kFuseStages, W = kThreads / 32;
   constexpr uint32_t G = T / 128;  // groups of 4 rows per lane
   static_assert(G <= 8, "a lane's pass mask holds 32 rows");

@@ -31,6 +31,7 @@ OUT = {"materialize": 0, "count": 1, "count_min": 2}
 FLAG_EAGER_ALL = 1
 FLAG_EAGER_ROOT = 2
 FLAG_TIMING = 4
+FLAG_TEST_TIMEOUT = 8
 CTR = {"cover_iters": 0, "probes": 1, "probe_hits": 2, "roots_built": 3, "subtries_forced": 4,
        "rows_regrouped": 5, "survivors": 6, "chunks": 7, "kernels": 8, "atom_built_mask": 9,
        "expand_ns": 10, "expand_launches": 11, "build_ns": 12, "span_ns": 13}
