@@ -13,7 +13,7 @@ outputs = COUNT), with the inputs resident in HBM; `e2e` repeats it through
 the public API from pinned host buffers.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fj|reference]
-                    [--workload star|rmat-triangle]
+                    [--workload star|rmat-triangle|batched|chooser]
 
 `--workload rmat-triangle` times the triangle count on the R-MAT graph of
 2^20 vertices and 2^24 edges instead (a second JSON line format, same keys).
@@ -638,6 +638,124 @@ def run_batched(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Fourth workload (--workload chooser): held-out 5-relation snowflake and
+# cycle queries run with the plain converted binary plan, the same plan with
+# the fewest-keys cover, and the order the learned chooser picks (its
+# network trained first, untimed, on work the engine reports for smaller
+# generated queries).
+# ---------------------------------------------------------------------------
+
+CHOOSER_METRIC = "tuples/sec (in+out), held-out snowflake/cycle queries, learned plan chooser"
+
+
+def run_chooser(args, rank, world):
+    import torch
+
+    from paper_2301_10841_gb300 import chooser as C
+    from paper_2301_10841_gb300 import fj
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = fj.Context(local)
+
+    def device(atoms):
+        return [{"rel": ctx.relation([torch.from_numpy(c).to(dev) for c in a["cols"]]),
+                 "vars": a["vars"]} for a in atoms]
+
+    t_train = time.perf_counter()
+    xs, ys = [], []
+    for q in range(120):
+        atoms, _ = G.chooser_query(q, 3_000, 20_000)
+        d = device(atoms)
+        hists = C.atom_histograms(atoms)
+        for o in C.candidate_orders([a["vars"] for a in atoms]):
+            r = fj.execute(ctx, d, fj.binary_to_free_plan(d, o, factor=True), out_mode="count")
+            xs.append(C.order_features(atoms, o, hists))
+            ys.append(np.log2(C.work(r) + 1.0))
+    x = np.stack(xs)
+    y = np.asarray(ys, dtype=np.float32)
+    scaler = C.fit_scaler(x)
+    model = fj.Model(ctx, C.IN_DIM, 128, 64, max_batch=8192)
+    model.set_params(C.init_params(C.IN_DIM, 128, 64, seed=1))
+    losses = C.train(model, torch.from_numpy(C.standardize(x, scaler)).to(dev),
+                     torch.from_numpy((y - y.mean()) / (y.std() + 1e-6)).to(dev))
+    t_train = time.perf_counter() - t_train
+
+    policies = {"plain": [], "fewest": [], "learned": []}
+    in_tuples = 0
+    for q in range(2000, 2000 + args.n_queries):
+        atoms, _ = G.chooser_query(q, args.min_rows, args.max_rows)
+        d = device(atoms)
+        in_tuples += sum(len(a["cols"][0]) for a in atoms)
+        orders = C.candidate_orders([a["vars"] for a in atoms])
+        chosen = C.choose(model, atoms, orders, C.atom_histograms(atoms), scaler)
+        declared = fj.binary_to_free_plan(d, orders[0], factor=True)
+        policies["plain"].append(fj.Prepared(ctx, d, declared, out_mode="count"))
+        policies["fewest"].append(fj.Prepared(ctx, d, declared, out_mode="count", cover="fewest"))
+        policies["learned"].append(fj.Prepared(ctx, d, fj.binary_to_free_plan(d, chosen, factor=True),
+                                               out_mode="count"))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def run(preps):
+        out = []
+        for p in preps:
+            p.reset()
+            out.append(p.execute().count)
+        return out
+
+    expect = run(policies["plain"])
+    for name in ("fewest", "learned"):
+        if run(policies[name]) != expect:
+            raise SystemExit(f"{name} results differ from the plain plan's")
+    out_tuples = sum(expect)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = {}
+    for name, preps in policies.items():
+        for _ in range(args.warmup):
+            run(preps)
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            got = run(preps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if got != expect:
+                raise SystemExit("result changed between steps")
+            times.append(e0.elapsed_time(e1))
+        ms[name] = sum(times) / len(times)
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    tot = in_tuples + out_tuples
+    line = {"metric": CHOOSER_METRIC, "value": tot / (ms["learned"] / 1000), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms["learned"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": f"{args.n_queries} held-out queries (datagen.chooser_query, "
+                                   f"seeds 2005..): 5-relation snowflakes and 5-cycles, rows "
+                                   f"log-uniform in [{args.min_rows}, {args.max_rows}], Zipf "
+                                   f"keys s in [0.8, 1.6]; COUNT(*)",
+                       "training": "120 generated queries of 3K-20K rows, every connected "
+                                   "order, label log2 engine work; 60 epochs on the library's "
+                                   "kernels",
+                       "l2": "flushed between steps (256 MB write)", "in_tuples": in_tuples},
+            "result": {"out_tuples": out_tuples},
+            "policies": {k: {"ms_per_step": v, "value": tot / (v / 1000)} for k, v in ms.items()},
+            "train": {"seconds": t_train, "samples": int(len(y)), "loss_first": losses[0],
+                      "loss_last": losses[-1]},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": None, "impl": "fj"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,7 +766,9 @@ def main():
     ap.add_argument("--n-fact", type=int, default=N_FACT)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="star", choices=["star", "rmat-triangle", "batched"])
+    ap.add_argument("--workload", default="star",
+                    choices=["star", "rmat-triangle", "batched", "chooser"])
+    ap.add_argument("--min-rows", type=int, default=50_000)
     ap.add_argument("--n-queries", type=int, default=256)
     ap.add_argument("--max-rows", type=int, default=2_000_000)
     args = ap.parse_args()
@@ -669,6 +789,8 @@ def main():
             run_rmat(args, rank, world)
         elif args.workload == "batched":
             run_batched(args, rank, world)
+        elif args.workload == "chooser":
+            run_chooser(args, rank, world)
         else:
             run_fj(args, rank, world)
     finally:
