@@ -46,3 +46,21 @@ def test_step_lowers_loss():
     for _ in range(50):
         _, theta = mlp.sgd_step(theta, x, t, d, h1, h2, 0.02)
     assert mlp.loss(theta, x, t, d, h1, h2) < 0.5 * l0
+
+
+def test_degree_histogram_definition():
+    from oracle import stats
+    # Full sample (mod 1): key k repeated 2^k times for k < 6 -> one key per
+    # bucket 0..5; degree estimate = count exactly.
+    col = np.concatenate([np.full(1 << k, k, dtype=np.int32) for k in range(6)])
+    h = stats.degree_histogram(col, mod=1)
+    np.testing.assert_allclose(h[:6], [1 / 6] * 6)
+    assert h[6:].sum() == 0
+    # Degree 3 lands in bucket 1, degree 4 in bucket 2 (floor of log2).
+    h = stats.degree_histogram(np.array([7, 7, 7, 9, 9, 9, 9], dtype=np.int32), mod=1)
+    np.testing.assert_allclose(h[1:3], [0.5, 0.5])
+    # The sample is the documented counter-based one: about 1 row in mod.
+    n = 20_000
+    picked = sum(stats.sample_hash(i, 5) % 100 == 0 for i in range(n))
+    assert 150 < picked < 250
+    assert stats.sample_hash(0, 0) == 0 and stats.sample_hash(1, 0) != 1
