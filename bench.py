@@ -669,7 +669,7 @@ def run_chooser(args, rank, world):
     for q in range(120):
         atoms, _ = G.chooser_query(q, 3_000, 20_000)
         d = device(atoms)
-        hists = C.atom_histograms(atoms)
+        hists = C.atom_histograms(ctx, atoms)
         for o in C.candidate_orders([a["vars"] for a in atoms]):
             r = fj.execute(ctx, d, fj.binary_to_free_plan(d, o, factor=True), out_mode="count")
             xs.append(C.order_features(atoms, o, hists))
@@ -690,7 +690,7 @@ def run_chooser(args, rank, world):
         d = device(atoms)
         in_tuples += sum(len(a["cols"][0]) for a in atoms)
         orders = C.candidate_orders([a["vars"] for a in atoms])
-        chosen = C.choose(model, atoms, orders, C.atom_histograms(atoms), scaler)
+        chosen = C.choose(model, atoms, orders, C.atom_histograms(ctx, atoms), scaler)
         declared = fj.binary_to_free_plan(d, orders[0], factor=True)
         policies["plain"].append(fj.Prepared(ctx, d, declared, out_mode="count"))
         policies["fewest"].append(fj.Prepared(ctx, d, declared, out_mode="count", cover="fewest"))

@@ -396,6 +396,19 @@ fj_status fj_model_train_step(fj_model* model, const float* d_x, const float* d_
 const char* fj_model_last_error(void);
 void fj_model_free(fj_model* model);
 
+/* Sampled key-degree histogram of one int32 device column (n < 2^31 rows),
+ * the chooser's feature (no counterpart in the paper).  Row i is sampled
+ * iff fmix32((i mod 2^32) xor seed) % mod == 0 (the 32-bit MurmurHash3
+ * finalizer); a key counted c times among the m sampled rows has estimated
+ * degree c n / m and lands in the largest bucket b < 32 with c n >= m 2^b;
+ * host_hist (32 floats) receives the fraction of distinct sampled keys per
+ * bucket (all zero when nothing is sampled).  Enqueued on the context's
+ * stream and synchronized.  Errors: FJ_ERR_INVALID_ARG, FJ_ERR_OOM,
+ * FJ_ERR_CUDA, with the reason in fj_stats_last_error(). */
+fj_status fj_degree_histogram(fj_ctx* ctx, const int32_t* d_col, uint64_t n, uint32_t mod,
+                              uint32_t seed, float* host_hist);
+const char* fj_stats_last_error(void);
+
 /* ------------------------------------------------------------------------ */
 /* Join without allocation (no counterpart in the paper)                     */
 /* ------------------------------------------------------------------------ */

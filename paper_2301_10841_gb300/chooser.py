@@ -5,8 +5,8 @@ own CUDA kernels) from sampled degree histograms.
 
 * Features of a candidate order (in_dim = 4 * 33 + 4): for each of its
   first four relations, log2 of the row count and the 32-bucket histogram of
-  log2 key degrees of the column it joins on (estimated from a seeded 1%
-  sample), then four shape scalars.
+  log2 key degrees of the column it joins on (fj.degree_histogram: a seeded,
+  counter-based 1% sample, on the GPU), then four shape scalars.
 * Label: log2 of the work the exact engine does on the plan (cover elements
   iterated plus probes, from its counters) -- deterministic, unlike a time.
 * Choice: the candidate with the smallest prediction; without a model, the
@@ -25,30 +25,17 @@ POSITIONS = 4
 IN_DIM = POSITIONS * (N_BUCKETS + 1) + 4
 
 
-def degree_histogram(col, frac=0.01, seed=0):
-    """Fraction of sampled keys per bucket floor(log2 degree), 32 buckets;
-    a key's degree is estimated as its count in the sample divided by frac."""
-    col = np.asarray(col)
-    n = len(col)
-    h = np.zeros(N_BUCKETS, dtype=np.float32)
-    if n == 0:
-        return h
-    m = max(1, int(n * frac))
-    rng = np.random.Generator(np.random.PCG64(seed))
-    sample = col[rng.integers(0, n, m)]
-    _, counts = np.unique(sample, return_counts=True)
-    deg = counts * (n / m)
-    b = np.clip(np.floor(np.log2(np.maximum(deg, 1.0))), 0, N_BUCKETS - 1).astype(np.int64)
-    np.add.at(h, b, 1.0)
-    return h / len(counts)
+def atom_histograms(ctx, atoms, seed=0):
+    """{(atom index, variable): the sampled key-degree histogram of that
+    atom's column (1% sample), from the library's kernel}."""
+    import torch
 
-
-def atom_histograms(atoms, seed=0):
-    """{(atom index, variable): histogram of that atom's column}."""
+    from paper_2301_10841_gb300 import fj
     out = {}
     for i, a in enumerate(atoms):
         for j, v in enumerate(a["vars"]):
-            out[(i, v)] = degree_histogram(a["cols"][j], seed=seed + 31 * i + j)
+            col = torch.from_numpy(np.ascontiguousarray(a["cols"][j], dtype=np.int32)).cuda()
+            out[(i, v)] = fj.degree_histogram(ctx, col, mod=100, seed=seed + 31 * i + j)
     return out
 
 

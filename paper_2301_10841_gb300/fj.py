@@ -132,6 +132,9 @@ _sig = {
                             ctypes.c_int),
     "fj_model_last_error": ([], ctypes.c_char_p),
     "fj_model_free": ([_vp], None),
+    "fj_degree_histogram": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vp],
+                            ctypes.c_int),
+    "fj_stats_last_error": ([], ctypes.c_char_p),
     "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
     "fj_result_free": ([_vp, _P(_Result)], None),
     "fj_join2_count_noalloc": ([_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp],
@@ -584,4 +587,16 @@ class Model:
             self.free()
         except Exception:
             pass
+
+
+def degree_histogram(ctx, col, mod=100, seed=0):
+    """fj_degree_histogram: the 32-bucket sampled key-degree histogram of an
+    int32 CUDA tensor, as a numpy float32 array."""
+    col = col.contiguous()
+    out = np.zeros(32, dtype=np.float32)
+    st = _lib.fj_degree_histogram(ctx.handle, _vp(col.data_ptr()), col.numel(), int(mod),
+                                  int(seed), _vp(out.ctypes.data))
+    if st != 0:
+        raise FJError(st, _lib.fj_stats_last_error().decode())
+    return out
 

@@ -53,7 +53,7 @@ def _engine_samples(fj, ctx, queries):
     out = []
     for atoms, _ in queries:
         dev, _ = device_atoms(fj, ctx, atoms)
-        hists = C.atom_histograms(atoms)
+        hists = C.atom_histograms(ctx, atoms)
         orders = C.candidate_orders([a["vars"] for a in atoms])
         rows = []
         for o in orders:
@@ -92,3 +92,17 @@ def test_chooser_gain(fj, ctx):
           f"chosen {tot_chosen:.1f}, best {tot_best:.1f}")
     assert tot_chosen < tot_declared
     model.free()
+
+
+def test_degree_histogram_kernel_matches_oracle(fj, ctx):
+    import torch
+
+    from oracle import stats
+    for seed, (n, s, mod) in enumerate([(50_000, 1.2, 100), (20_000, 0.8, 7), (3_000, 1.6, 1)]):
+        rng = np.random.default_rng(seed)
+        col = G.zipf_ranks(n // 3, s, n, rng).astype(np.int32) - (n // 6)
+        got = fj.degree_histogram(ctx, torch.from_numpy(col).cuda(), mod=mod, seed=seed)
+        want = stats.degree_histogram(col, mod=mod, seed=seed)
+        np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-7)
+    empty = fj.degree_histogram(ctx, torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert not empty.any()
