@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <set>
 #include <string>
@@ -280,13 +281,30 @@ void launch_expand_r(fj_prepared* P, int grid, const NodeDev& nd) {
     k_expand_static<R><<<grid, kThreads, P->smem_expand, c->stream>>>(nd, P->d_atoms, P->d_res);
 }
 
+constexpr int kMaxDevicesAttr = 64;
+
 template <int R>
 void expand_attrs(size_t smem, int* blocks) {
   const void* fns[2] = {reinterpret_cast<const void*>(&k_expand<R>),
                         reinterpret_cast<const void*>(&k_expand_static<R>)};
+  // The dynamic shared memory limit is one setting per kernel (and device)
+  // for the whole process: only ever raise it, so a prepared plan needing
+  // less never lowers it under one needing more.
+  static std::mutex mu;
+  static size_t limit[kMaxDevicesAttr] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[dev < kMaxDevicesAttr && dev >= 0 ? dev : 0];
+    if (smem > cur) {
+      for (const void* fn : fns)
+        CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+      cur = smem;
+    }
+  }
   *blocks = 1 << 20;
   for (const void* fn : fns) {
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int b = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, smem));
     *blocks = std::min(*blocks, std::max(1, b));

@@ -101,17 +101,24 @@ fj_status fj_degree_histogram(fj_ctx* ctx, const int32_t* d_col, uint64_t n, uin
   const uint64_t expect = n / mod + 64;
   uint32_t cap = 64;
   while (uint64_t(cap) < 4 * expect && cap < (1u << 30)) cap <<= 1;
-  unsigned long long* buf = nullptr;  // slots, n_sampled, hist[33]
+  unsigned long long* buf = nullptr;  // slots, n_sampled, hist[33], status
   const size_t words = size_t(cap) + 1 + 33;
-  if (cudaMallocAsync(&buf, words * 8 + 4, s) != cudaSuccess)
+  // Plain allocation: this runs once per column, outside any timed path,
+  // and must leave no pending error behind for the caller's next launch.
+  if (cudaMalloc(&buf, words * 8 + 8) != cudaSuccess) {
+    cudaGetLastError();
     return stats_fail(FJ_ERR_OOM, "histogram scratch");
+  }
   uint32_t* status = reinterpret_cast<uint32_t*>(buf + words);
   unsigned long long host[34];
   uint32_t st = 0;
-  cudaError_t e = cudaMemsetAsync(buf, 0, words * 8 + 4, s);
+  cudaError_t e = cudaMemsetAsync(buf, 0, words * 8 + 8, s);
   if (e == cudaSuccess) {
     int g = int(std::min<uint64_t>((n + kT - 1) / kT, 4096));
     k_hist_count<<<g, kT, 0, s>>>(d_col, n, mod, seed, buf, cap - 1, buf + cap, status);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
     int g2 = int(std::min<uint64_t>((cap + kT - 1) / kT, 1024));
     k_hist_bucket<<<g2, kT, 0, s>>>(buf, cap, n, buf + cap, buf + cap + 1);
     e = cudaGetLastError();
@@ -119,7 +126,9 @@ fj_status fj_degree_histogram(fj_ctx* ctx, const int32_t* d_col, uint64_t n, uin
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf + cap + 1, 33 * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFreeAsync(buf, s);
+  const cudaError_t ef = cudaFree(buf);
+  if (e == cudaSuccess) e = ef;
+  cudaGetLastError();  // reported below, not left for the next launch
   if (e != cudaSuccess) return stats_fail(FJ_ERR_CUDA, cudaGetErrorString(e));
   if (st) return stats_fail(FJ_ERR_CUDA, "histogram table overfilled");
   if (host[32])
