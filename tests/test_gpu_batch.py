@@ -4,7 +4,6 @@ eagerly and as one captured CUDA graph (replayed twice); a query whose
 output size the host would decide (materialized output) is refused with
 FJ_ERR_UNSUPPORTED."""
 
-import numpy as np
 import pytest
 
 import oracle

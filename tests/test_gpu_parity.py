@@ -8,7 +8,6 @@ import pytest
 
 import oracle
 from oracle import closed
-from oracle import plan as P
 from paper_2301_10841_gb300 import datagen as G
 
 from fjtest import device_atoms, gj_plan, plans_for, sort_rows
