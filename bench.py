@@ -45,6 +45,8 @@ N_FACT = 10_000_000
 THETA = G.STAR_THETA
 MIN_VARS = [4, 5, 6, 7]
 L2_FLUSH_BYTES = 256 << 20
+L2_NOTE = ("flushed between steps: a 256 MB buffer written, then a second 256 MB buffer read, "
+           "so the step starts with a cold L2 holding no dirty lines")
 RESULT_D2H_BYTES = 8 + 4 * 32 + 8 + 4 + 4 + 8 * 16  # the library's result block
 
 
@@ -55,9 +57,24 @@ def workload_config(n_fact=N_FACT):
                     f"uniform [0,1e9)), selection attr < 1e8; COUNT(*) + MIN(a1..a4)",
         "plan": "factor(binary2fj([F,D1,D2,D3,D4])), static cover, batch 2048",
         "seed": 2,
-        "l2": "flushed between steps (256 MB write)",
+        "l2": L2_NOTE,
         "in_tuples": n_fact + sum(DIMS),
     }
+
+
+class L2Flush:
+    """Evicts the L2 between timed steps: writes a buffer larger than the L2,
+    then reads a second one, so the dirty lines of the write are written back
+    before the next timed region instead of during it."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        self.r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def zero_(self):
+        self.w.zero_()
+        self.r.max()
 
 
 # ---------------------------------------------------------------------------
@@ -184,21 +201,49 @@ def profiled_traffic(kernel_hash):
 # CPU baseline (the oracle) -- the only place bench.py runs oracle/.
 # ---------------------------------------------------------------------------
 
-def oracle_sample(fact, dims, budget_s=12.0, start_rows=250_000):
-    """Time the oracle's left-deep hash join on a prefix of F (full
-    dimensions), growing the prefix until one run takes a few seconds, and
-    scale repetitions to about `budget_s` of CPU work."""
+def _oracle_join_parallel(fact, dims, n, cores):
+    """The oracle's binary join with its outer loop (the fact rows) split
+    into `cores` contiguous parts run on as many host threads (ctypes drops
+    the GIL during each call); counts add up and MINs take the least."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    bounds = [n * i // cores for i in range(cores + 1)]
+    parts = [G.star_query({"name": "F", "cols": [c[a:b] for c in fact["cols"]]}, dims,
+                          theta=THETA) for a, b in zip(bounds, bounds[1:]) if b > a]
+    with ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        res = list(ex.map(lambda q: oracle.binary_join(q, min_vars=MIN_VARS), parts))
+    cnt = sum(r[0] for r in res)
+    mins = []
+    for i in range(len(MIN_VARS)):
+        vals = [r[1][i] for r in res if r[1][i] is not None]
+        mins.append(min(vals) if vals else None)
+    return cnt, mins
+
+
+def cpu_baseline_leg(fact, dims, budget_s=12.0, start_rows=250_000):
+    """The oracle on the host cores -- the only part of the star workload
+    that runs oracle/.
+
+    (i) single thread: the oracle's left-deep hash join on a prefix of F
+    (full dimensions), the prefix grown until one run takes a few seconds
+    (the whole of F when that is quicker), repeated for about `budget_s`;
+    (ii) the same join with F split over every host core.
+    Also returns the exact result on the whole of F, computed twice:
+    by the oracle's hash join and by the direct-address semi-join of
+    `oracle.closed`, for the parity check of the GPU result."""
+    import oracle
+    from oracle import closed
     oracle.build()
     n = start_rows
+    n_all = len(fact["cols"][0])
     while True:
         q = G.star_query({"name": "F", "cols": [c[:n] for c in fact["cols"]]}, dims, theta=THETA)
         t0 = time.perf_counter()
         cnt, mins, _ = oracle.binary_join(q, min_vars=MIN_VARS)
         dt = time.perf_counter() - t0
-        if dt > 2.0 or n >= len(fact["cols"][0]):
+        if dt > 2.0 or n >= n_all:
             break
-        n = min(len(fact["cols"][0]), n * 4)
+        n = min(n_all, n * 4)
     reps = max(1, int(budget_s / max(dt, 1e-3)))
     times = [dt]
     for _ in range(reps - 1):
@@ -207,10 +252,32 @@ def oracle_sample(fact, dims, budget_s=12.0, start_rows=250_000):
         times.append(time.perf_counter() - t0)
     tin = n + sum(len(d["cols"][0]) for d in dims)
     tps = (tin + cnt) / statistics.median(times)
-    return {"value": tps, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"hash binary join (oracle O1, single thread) on the first {n} fact rows "
-                      f"with full dimensions, median of {len(times)} runs",
-            "seconds": sum(times)}
+    cores = os.cpu_count() or 1
+    ptimes = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        pcnt, pmins = _oracle_join_parallel(fact, dims, n, cores)
+        ptimes.append(time.perf_counter() - t0)
+    if (pcnt, pmins) != (cnt, mins):
+        raise SystemExit(f"oracle: split join {(pcnt, pmins)} differs from {(cnt, mins)}")
+    ptps = (tin + cnt) / statistics.median(ptimes)
+    cpu = {"value": tps, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"hash binary join (oracle O1, single thread) on the first {n} fact rows "
+                     f"with full dimensions, median of {len(times)} runs",
+           "seconds": sum(times),
+           "all_cores": {"value": ptps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"the same join with the {n} fact rows split into {cores} "
+                                   f"parts on {cores} host threads (nproc), median of "
+                                   f"{len(ptimes)} runs", "seconds": sum(ptimes)}}
+    # The exact result over the whole of F.
+    if n < n_all:
+        qa = G.star_query(fact, dims, theta=THETA)
+        cnt, mins, _ = oracle.binary_join(qa, min_vars=MIN_VARS)
+    dcnt, dmins = closed.star_join_direct(fact["cols"], [d["cols"] for d in dims],
+                                          [THETA] * len(dims))
+    exact = {"oracle_binary_join": {"count": cnt, "mins": mins},
+             "direct_address": {"count": dcnt, "mins": dmins}, "fact_rows": n_all}
+    return cpu, exact
 
 
 def run_reference(args, rank, world):
@@ -268,7 +335,7 @@ def run_fj(args, rank, world):
     plan = fj.binary_to_free_plan(atoms, [0, 1, 2, 3, 4], factor=True)
     prep = fj.Prepared(ctx, atoms, plan, out_mode="count_min", min_vars=MIN_VARS,
                        batch_size=args.batch, flags=fj.FLAG_TIMING)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -356,18 +423,24 @@ def run_fj(args, rank, world):
                 "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
                 "traffic": profiled_traffic(khash), "algorithmic_bytes": alg,
                 "launch_us": launch_s * 1e6, "kernel_source": khash}
-    cpu = None
+    cpu, parity = None, None
     if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_sample(fact, dims)
+        cpu, exact = cpu_baseline_leg(fact, dims)
+        got = {"count": expect[0], "mins": list(expect[1])}
+        ok = all(got == e for e in (exact["oracle_binary_join"], exact["direct_address"]))
+        parity = {"exact": ok, "gpu": got, **exact}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
             "data": "synthetic", "config": workload_config(args.n_fact),
             "result": {"count": expect[0], "mins": expect[1], "survivors": survivors},
+            "parity": parity,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "counters": res.counters,
             "gpu_launches": kernels, "impl": "fj"}
     print(json.dumps(line), flush=True)
+    if parity is not None and not parity["exact"]:
+        raise SystemExit("the GPU result differs from the oracle's on the full workload")
 
 
 # ---------------------------------------------------------------------------
@@ -397,7 +470,7 @@ def run_rmat(args, rank, world):
     atoms = [{"rel": rel, "vars": a["vars"], "rel_cols": a["rel_cols"]} for a in q]
     prep = fj.Prepared(ctx, atoms, TRI_PLAN, out_mode="count", cover="fewest",
                        flags=fj.FLAG_TIMING)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         prep.reset()
@@ -482,7 +555,7 @@ def run_rmat(args, rank, world):
                                    f"{n_edges} distinct directed edges without self-loops, "
                                    f"seed 3; triangle count Q(x,y,z) :- E(x,y),E(y,z),E(z,x)",
                        "plan": "[[E1(x,y),E2(y),E3(x)],[E2(z),E3(z)]], fewest-keys cover",
-                       "l2": "flushed between steps (256 MB write)",
+                       "l2": L2_NOTE,
                        "in_tuples": 3 * n_edges},
             "result": {"count": expect},
             "roofline": {"bound": "hbm", "kernel": "whole step (every launch)",
@@ -549,7 +622,7 @@ def run_batched(args, rank, world):
         except fj.FJError:
             single.append(i)
     batch = fj.Batch(ctx, [tuned[i] for i in graphed], graph=True)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     def step_batched():
@@ -621,7 +694,7 @@ def run_batched(args, rank, world):
                        "plan": "factor(binary2fj(order)) per query, autotuned cover-batch "
                                "size and load factor",
                        "graphed_queries": len(graphed), "single_queries": len(single),
-                       "l2": "flushed between steps (256 MB write)", "in_tuples": in_tuples},
+                       "l2": L2_NOTE, "in_tuples": in_tuples},
             "result": {"out_tuples": out_tuples},
             "plain": {"ms_per_step": ms_plain,
                       "value": per_rank * world / (ms_plain / 1000),
@@ -696,7 +769,7 @@ def run_chooser(args, rank, world):
         policies["fewest"].append(fj.Prepared(ctx, d, declared, out_mode="count", cover="fewest"))
         policies["learned"].append(fj.Prepared(ctx, d, fj.binary_to_free_plan(d, chosen, factor=True),
                                                out_mode="count"))
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     def run(preps):
@@ -746,7 +819,7 @@ def run_chooser(args, rank, world):
                        "training": "120 generated queries of 3K-20K rows, every connected "
                                    "order, label log2 engine work; 60 epochs on the library's "
                                    "kernels",
-                       "l2": "flushed between steps (256 MB write)", "in_tuples": in_tuples},
+                       "l2": L2_NOTE, "in_tuples": in_tuples},
             "result": {"out_tuples": out_tuples},
             "policies": {k: {"ms_per_step": v, "value": tot / (v / 1000)} for k, v in ms.items()},
             "train": {"seconds": t_train, "samples": int(len(y)), "loss_first": losses[0],

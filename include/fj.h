@@ -431,9 +431,10 @@ const char* fj_stats_last_error(void);
  * call on a device looks up that array's device address (cudaGetSymbolAddress
  * with the device current); make that first call before any stream capture.
  * All calls share the array: each clears what it uses, and calls that
- * overlap on the GPU (other streams or threads) race.  Errors:
- * FJ_ERR_INVALID_ARG, FJ_ERR_CUDA, with the reason in
- * fj_noalloc_last_error(). */
+ * overlap on the GPU (other streams or threads) race.  A CUDA error already
+ * pending when the call starts is reported as FJ_ERR_CUDA and left pending
+ * (nothing is launched).  Errors: FJ_ERR_INVALID_ARG, FJ_ERR_CUDA, with the
+ * reason in fj_noalloc_last_error(). */
 fj_status fj_join2_count_noalloc(const int32_t* d_r_key, uint64_t n_r,
                                  const int32_t* d_s_key, uint64_t n_s,
                                  uint64_t* d_count, void* cuda_stream);

@@ -73,3 +73,57 @@ def star_join_direct(fact_cols, dims, thresholds):
     count = int(mult.sum(dtype=np.uint64))
     mins = [int(l[live].min()) if live.any() else None for l in lows]
     return count, mins
+
+
+def pkfk_direct(atoms, min_vars=()):
+    """COUNT and MIN of a full conjunctive query whose atoms form a tree of
+    primary-key / foreign-key links, by direct addressing -- the semi-join
+    composition "follow each foreign key to its key row" (no hash table).
+
+    The first atom is the root.  Every later atom shares exactly one
+    variable with the atoms before it, read from its own first column, and
+    that column holds distinct non-negative keys (its primary key); its other
+    variables are its own.  An atom's pushed-down selections remove its rows
+    before addressing.  For every root row passing its selections, the row
+    of each later atom is found by addressing that atom's key array with the
+    value of the shared variable in the row reached so far; the root row
+    contributes one output tuple iff every atom has such a row (keys are
+    unique, so no more than one).  Returns (count, mins) with None for an
+    empty result.
+    """
+    ops = {"<": np.less, "<=": np.less_equal, ">": np.greater, ">=": np.greater_equal,
+           "==": np.equal, "!=": np.not_equal}
+
+    def passing(a):
+        n = len(a["cols"][0]) if a["cols"] else 0
+        ok = np.ones(n, dtype=bool)
+        for j, op, v in a.get("preds", []):
+            ok &= ops[op](np.asarray(a["cols"][j], dtype=np.int64), v)
+        return ok
+
+    root = atoms[0]
+    n = len(root["cols"][0])
+    alive = passing(root)
+    # value of each bound variable for every root row (rows of later atoms
+    # gathered through their keys)
+    val = {v: np.asarray(c, dtype=np.int64) for v, c in zip(root["vars"], root["cols"])}
+    for a in atoms[1:]:
+        shared = [v for v in a["vars"] if v in val]
+        assert len(shared) == 1 and a["vars"][0] == shared[0], "not a key/foreign-key tree"
+        key = np.asarray(a["cols"][0], dtype=np.int64)
+        assert len(np.unique(key)) == len(key) and (len(key) == 0 or key.min() >= 0)
+        size = int(key.max()) + 1 if len(key) else 0
+        ok = passing(a)
+        row_of = np.full(size + 1, -1, dtype=np.int64)  # slot `size`: no row
+        row_of[key[ok]] = np.nonzero(ok)[0]
+        fk = val[shared[0]]
+        inside = (fk >= 0) & (fk < size)
+        r = row_of[np.where(inside, fk, size)]
+        alive &= r >= 0
+        rr = np.where(r >= 0, r, 0)
+        for v, c in zip(a["vars"][1:], a["cols"][1:]):
+            c = np.asarray(c, dtype=np.int64)
+            val[v] = c[rr] if len(c) else np.zeros(n, dtype=np.int64)
+    count = int(alive.sum())
+    mins = [int(val[v][alive].min()) if count else None for v in min_vars]
+    return count, mins

@@ -107,6 +107,11 @@ fj_status fail(fj_status st, const char* msg) {
   return st;
 }
 
+fj_status fail_cuda(const char* what, cudaError_t e) {
+  snprintf(g_err, sizeof(g_err), "fj_join2_count_noalloc: %s: %s", what, cudaGetErrorString(e));
+  return FJ_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -123,6 +128,10 @@ fj_status fj_join2_count_noalloc(const int32_t* d_r_key, uint64_t n_r, const int
     return fail(FJ_ERR_INVALID_ARG,
                 "fj_join2_count_noalloc: S has more than 524288 rows (the fixed scratch "
                 "table holds 1048576 slots at load factor 1/2)");
+  // An error left pending by the caller's earlier work is reported as such
+  // and left in place (not consumed, not blamed on this call's launches).
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) return fail_cuda("a CUDA error was pending before the call", pending);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(FJ_ERR_CUDA, "fj_join2_count_noalloc: no current CUDA device");
@@ -134,8 +143,8 @@ fj_status fj_join2_count_noalloc(const int32_t* d_r_key, uint64_t n_r, const int
     if (!g_addr[dev]) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-      if (e != cudaSuccess || !p)
-        return fail(FJ_ERR_CUDA, "fj_join2_count_noalloc: cudaGetSymbolAddress failed");
+      if (e != cudaSuccess) return fail_cuda("cudaGetSymbolAddress", e);
+      if (!p) return fail(FJ_ERR_CUDA, "fj_join2_count_noalloc: cudaGetSymbolAddress gave NULL");
       g_addr[dev] = static_cast<unsigned long long*>(p);
     }
     slots = g_addr[dev];
@@ -146,17 +155,21 @@ fj_status fj_join2_count_noalloc(const int32_t* d_r_key, uint64_t n_r, const int
   int grid_c = int((cap + kThreads - 1) / kThreads);
   if (grid_c > 4096) grid_c = 4096;
   k_na_clear<<<grid_c, kThreads, 0, s>>>(slots, cap, reinterpret_cast<unsigned long long*>(d_count));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda("clear launch", e);
   if (n_s) {
     uint64_t g = (n_s + kThreads - 1) / kThreads;
     k_na_build<<<int(g < 4096 ? g : 4096), kThreads, 0, s>>>(slots, cap - 1, d_s_key, n_s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda("build launch", e);
   }
   if (n_r) {
     uint64_t g = (n_r + kThreads - 1) / kThreads;
     k_na_probe<<<int(g < 4096 ? g : 4096), kThreads, 0, s>>>(
         slots, cap - 1, d_r_key, n_r, reinterpret_cast<unsigned long long*>(d_count));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda("probe launch", e);
   }
-  if (cudaGetLastError() != cudaSuccess)
-    return fail(FJ_ERR_CUDA, "fj_join2_count_noalloc: kernel launch failed");
   return FJ_OK;
 }
 

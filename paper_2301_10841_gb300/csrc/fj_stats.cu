@@ -96,6 +96,12 @@ fj_status fj_degree_histogram(fj_ctx* ctx, const int32_t* d_col, uint64_t n, uin
     return stats_fail(FJ_ERR_INVALID_ARG, "bad histogram arguments");
   if (n >= (1ull << 31)) return stats_fail(FJ_ERR_INVALID_ARG, "column above 2^31 rows");
   for (int b = 0; b < 32; ++b) host_hist[b] = 0.f;
+  // An error left pending by the caller's earlier work is reported and left
+  // in place: the error reads below then only ever see this call's own.
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return stats_fail(FJ_ERR_CUDA, std::string("a CUDA error was pending before the call: ") +
+                                       cudaGetErrorString(pending));
   if (n == 0) return FJ_OK;
   cudaStream_t s = fj_internal_ctx_stream(ctx);
   const uint64_t expect = n / mod + 64;

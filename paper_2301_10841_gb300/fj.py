@@ -403,6 +403,19 @@ def join2_count_noalloc(r_key, s_key, out, stream=None):
     with no device allocation (fj_join2_count_noalloc).  `r_key` and `s_key`
     are contiguous int32 CUDA tensors; work goes on `stream` (default: the
     current torch stream) and is not waited for."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("r_key", r_key, torch.int32), ("s_key", s_key, torch.int32),
+                        ("out", out, torch.int64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt:
+            raise ValueError(f"{name} must be a {dt} CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, not the current device "
+                             f"cuda:{dev}")
+    if out.numel() < 1:
+        raise ValueError("out must hold at least one element")
     if stream is None:
         stream = _current_stream()
     st = _lib.fj_join2_count_noalloc(_vp(r_key.data_ptr()), r_key.numel(),
@@ -592,6 +605,11 @@ class Model:
 def degree_histogram(ctx, col, mod=100, seed=0):
     """fj_degree_histogram: the 32-bucket sampled key-degree histogram of an
     int32 CUDA tensor, as a numpy float32 array."""
+    import torch
+    if not isinstance(col, torch.Tensor) or not col.is_cuda or col.dtype != torch.int32:
+        raise ValueError("col must be an int32 CUDA tensor")
+    if col.device.index != ctx.device:
+        raise ValueError(f"col is on cuda:{col.device.index}, the context on cuda:{ctx.device}")
     col = col.contiguous()
     out = np.zeros(32, dtype=np.float32)
     st = _lib.fj_degree_histogram(ctx.handle, _vp(col.data_ptr()), col.numel(), int(mod),

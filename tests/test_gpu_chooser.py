@@ -19,6 +19,11 @@ pytestmark = pytest.mark.gpu
 
 
 def test_model_kernels_match_oracle(fj, ctx):
+    """Forward within 1e-5 relative to each output's magnitude (the sum of
+    the absolute values of its terms, mlp.magnitudes); every gradient
+    element against the float64 chain rule and a float32 CPU backprop within
+    1e-4 of its own magnitude, and against central finite differences of the
+    float64 loss within 1e-3 relative; descent steps follow float64."""
     import torch
     d, h1, h2, n = C.IN_DIM, 128, 64, 700
     rng = np.random.default_rng(11)
@@ -29,20 +34,47 @@ def test_model_kernels_match_oracle(fj, ctx):
     assert m.n_params == mlp.n_params(d, h1, h2)
     m.set_params(theta)
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
-    y = m.forward(xd).cpu().numpy()
-    want, _ = mlp.forward(theta.astype(np.float64), x, d, h1, h2)
-    np.testing.assert_allclose(y, want, rtol=1e-4, atol=1e-4)
+    th64 = theta.astype(np.float64)
+    y = m.forward(xd).cpu().numpy().astype(np.float64)
+    want, _ = mlp.forward(th64, x, d, h1, h2)
+    ymag, gmag = mlp.magnitudes(th64, x, t, d, h1, h2)
+    assert np.all(np.abs(y - want) <= 1e-5 * ymag), np.max(np.abs(y - want) / ymag)
     g, loss = m.gradients(xd, td)
-    g_want = mlp.gradients(theta.astype(np.float64), x, t, d, h1, h2)
-    assert np.linalg.norm(g - g_want) <= 1e-4 * np.linalg.norm(g_want)
-    assert abs(loss - mlp.loss(theta.astype(np.float64), x, t, d, h1, h2)) <= 1e-4 * loss
+    g = g.astype(np.float64)
+    g64 = mlp.gradients(th64, x, t, d, h1, h2)
+    g32 = mlp.gradients(theta, x, t, d, h1, h2, dtype=np.float32).astype(np.float64)
+    tiny = 1e-12
+    assert np.all(np.abs(g - g64) <= 1e-4 * gmag + tiny), np.max(np.abs(g - g64) / (gmag + tiny))
+    assert np.all(np.abs(g - g32) <= 1e-4 * gmag + tiny), np.max(np.abs(g - g32) / (gmag + tiny))
+    assert abs(loss - mlp.loss(th64, x, t, d, h1, h2)) <= 1e-5 * loss
+    # Central finite differences of the float64 loss, every parameter of a
+    # smaller network (the same kernels, other shapes).
+    ds, hs1, hs2, ns = 24, 16, 8, 48
+    ths = C.init_params(ds, hs1, hs2, seed=5) + np.float32(0.01)
+    xs = rng.normal(0, 1, (ns, ds)).astype(np.float32)
+    ts = rng.normal(0, 1, ns).astype(np.float32)
+    ms = fj.Model(ctx, ds, hs1, hs2, max_batch=64)
+    ms.set_params(ths)
+    gs, _ = ms.gradients(torch.from_numpy(xs).cuda(), torch.from_numpy(ts).cuda())
+    th = ths.astype(np.float64)
+    eps = 1e-6
+    fd = np.empty_like(th)
+    for i in range(len(th)):
+        e = np.zeros_like(th)
+        e[i] = eps
+        fd[i] = (mlp.loss(th + e, xs, ts, ds, hs1, hs2) -
+                 mlp.loss(th - e, xs, ts, ds, hs1, hs2)) / (2 * eps)
+    floor = 1e-3 * np.max(np.abs(fd))
+    rel = np.abs(gs - fd) / np.maximum(np.abs(fd), floor)
+    assert np.all(rel < 1e-3), (np.argmax(rel), rel.max())
+    ms.free()
     # Twenty descent steps follow the float64 trajectory.
-    th = theta.astype(np.float64)
+    th = th64
     for _ in range(20):
         l_gpu = m.train_step(xd, td, 0.01)
         l_cpu, th = mlp.sgd_step(th, x, t, d, h1, h2, 0.01)
-        assert abs(l_gpu - l_cpu) <= 1e-3 * l_cpu
-    np.testing.assert_allclose(m.params(), th, rtol=1e-3, atol=1e-4)
+        assert abs(l_gpu - l_cpu) <= 1e-4 * l_cpu
+    np.testing.assert_allclose(m.params(), th, rtol=1e-3, atol=1e-5)
     with pytest.raises(fj.FJError):
         m.forward(torch.zeros((1025, d), device="cuda"))
     m.free()

@@ -68,6 +68,54 @@ def test_sharded_star_join_merges_to_the_whole(tmp_path):
     assert (got["count"], got["mins"]) == (c, m)
 
 
+def _merge_edges_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    from paper_2301_10841_gb300 import shard
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    got = {}
+    # A true MIN of 2^31 - 1 on one rank, no result row on the other.
+    c, m = (5, [2**31 - 1, -3]) if rank == 0 else (0, [None, None])
+    got["int32_max"] = shard.merge(c, m)
+    # Counts above 2^63 (uint64): their sum still fits.
+    got["big"] = shard.merge(2**63 - 1 + rank, [rank])
+    # A sum of 2^64 does not fit.
+    try:
+        shard.merge(2**63, [0])
+        got["overflow"] = False
+    except OverflowError:
+        got["overflow"] = True
+    if rank == 0:
+        with open(out, "w") as f:
+            json.dump(got, f)
+    dist.destroy_process_group()
+
+
+def test_merge_keeps_int32_max_and_uint64_counts(tmp_path):
+    """The merge's edge cases: a MIN equal to 2^31 - 1 is a value, not "no
+    row"; counts above 2^63 merge exactly; a total of 2^64 is an overflow."""
+    import multiprocessing as mp
+
+    out = str(tmp_path / "edges.json")
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_merge_edges_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    with open(out) as f:
+        got = json.load(f)
+    assert got["int32_max"] == [5, [2**31 - 1, -3]]
+    assert got["big"] == [2**64 - 1, [0]]
+    assert got["overflow"] is True
+
+
 def test_bench_reference_arm_two_ranks():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",

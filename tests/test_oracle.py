@@ -243,3 +243,30 @@ def test_factor_never_breaks_validity_on_random_queries():
         plan = P.binary2fj(atom_vars, order)
         assert P.is_valid(atom_vars, plan)
         assert P.is_valid(atom_vars, P.factor(plan))
+
+
+def test_pkfk_direct_equals_hash_join_on_batch_queries():
+    """closed.pkfk_direct (follow every foreign key to its key row by direct
+    addressing) equals the oracle's hash join on chains and stars of the
+    batched workload, small sizes, with selections and empty results."""
+    from oracle import closed
+    n_empty = 0
+    for q in range(40):
+        atoms, _, mins = G.batch_query(q, min_rows=50, max_rows=4000)
+        want = oracle.binary_join(atoms, min_vars=mins)[:2]
+        got = closed.pkfk_direct(atoms, mins)
+        assert got == (want[0], want[1]), q
+        n_empty += want[0] == 0
+    assert n_empty < 40
+
+
+def test_pkfk_direct_catches_a_wrong_key():
+    """A planted mistake (one key row renumbered) changes the result."""
+    from oracle import closed
+    atoms, _, mins = G.batch_query(3, min_rows=500, max_rows=2000)
+    base = closed.pkfk_direct(atoms, mins)
+    bad = [dict(a) for a in atoms]
+    key = np.array(bad[1]["cols"][0], copy=True)
+    key = key[::-1].copy()  # keys still unique, rows now point elsewhere
+    bad[1]["cols"] = [key] + list(bad[1]["cols"][1:])
+    assert closed.pkfk_direct(bad, mins) != base
