@@ -13,7 +13,7 @@ outputs = COUNT), with the inputs resident in HBM; `e2e` repeats it through
 the public API from pinned host buffers.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fj|reference]
-                    [--workload star|rmat-triangle|batched|chooser]
+                    [--workload star|rmat-triangle|batched|chooser|ablation]
 
 `--workload rmat-triangle` times the triangle count on the R-MAT graph of
 2^20 vertices and 2^24 edges instead (a second JSON line format, same keys).
@@ -55,7 +55,8 @@ def workload_config(n_fact=N_FACT):
         "workload": f"star join: F {n_fact} rows x 4 int32 FK Zipf(1.1) via seeded permutation; "
                     f"D1..D4 = {'/'.join(str(d) for d in DIMS)} rows (int32 key, int32 attr "
                     f"uniform [0,1e9)), selection attr < 1e8; COUNT(*) + MIN(a1..a4)",
-        "plan": "factor(binary2fj([F,D1,D2,D3,D4])), static cover, batch 2048",
+        "plan": "factor(binary2fj([F,D1,D2,D3,D4])), static cover, batch 1024",
+        "launch": "one CUDA graph launch per step (the execution captured once)",
         "seed": 2,
         "l2": L2_NOTE,
         "in_tuples": n_fact + sum(DIMS),
@@ -335,16 +336,15 @@ def run_fj(args, rank, world):
     plan = fj.binary_to_free_plan(atoms, [0, 1, 2, 3, 4], factor=True)
     prep = fj.Prepared(ctx, atoms, plan, out_mode="count_min", min_vars=MIN_VARS,
                        batch_size=args.batch, flags=fj.FLAG_TIMING)
+    # One step = one launch of a CUDA graph holding the whole execution from
+    # the base tables (COLT state reset, root build, node 0), captured once.
+    batch = fj.Batch(ctx, [prep], graph=True)
     flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        prep.reset()
-        prep.execute_async()
-
     for _ in range(args.warmup):
-        step()
-        ref = prep.result()
+        batch.launch()
+        ref = batch.results()[0]
     expect = (ref.count, ref.mins)
 
     if world > 1:
@@ -358,9 +358,9 @@ def run_fj(args, rank, world):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        batch.launch()
         e1.record(stream)
-        res = prep.result()
+        res = batch.results()[0]
         torch.cuda.synchronize()
         if (res.count, res.mins) != expect:
             raise SystemExit(f"result changed between steps: {(res.count, res.mins)} vs {expect}")
@@ -829,18 +829,137 @@ def run_chooser(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Fifth workload (--workload ablation): the paper's COLT and vectorization
+# ablations (Section 5.3) and its Generic Join baseline (Section 5.1), on the
+# same GPU.  Tries: COLT (lazy), simple lazy trie (every root built eagerly)
+# and simple trie (every level built eagerly); batch sizes of the general
+# node kernel (cover elements per block round: 256 is one per thread, the
+# tuple-at-a-time end; 4096 is sixteen per thread with their loads in flight
+# together); Generic Join: one node per variable, every trie built eagerly,
+# the smallest batch, no one-launch node-0 scan.
+# ---------------------------------------------------------------------------
+
+ABL_METRIC = "ms per query (lower is better), COLT and vectorization ablations, FJ vs GJ"
+
+
+def _time_prepared(prep, flush, stream, steps, warmup):
+    import torch
+    out = None
+    for _ in range(warmup):
+        prep.reset()
+        out = prep.execute()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prep.reset()
+        prep.execute_async()
+        e1.record(stream)
+        r = prep.result()
+        torch.cuda.synchronize()
+        if (r.count, r.mins) != (out.count, out.mins):
+            raise SystemExit("ablation: result changed between steps")
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times), out
+
+
+def run_ablation(args, rank, world):
+    import torch
+
+    from paper_2301_10841_gb300 import fj
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = fj.Context(local)
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream()
+    steps, warmup = max(2, min(args.steps, 10)), 3
+    rows = []
+
+    def sweep(name, atoms, fj_plan, gj_plan, out_mode, min_vars, cover):
+        base = None
+        cfgs = [("colt", "default", fj_plan, 0, 0, cover),
+                ("colt", 256, fj_plan, 256, fj.FLAG_NO_FUSED_SCAN, cover),
+                ("colt", 1024, fj_plan, 1024, fj.FLAG_NO_FUSED_SCAN, cover),
+                ("colt", 4096, fj_plan, 4096, fj.FLAG_NO_FUSED_SCAN, cover),
+                ("simple_lazy_trie", "default", fj_plan, 0, fj.FLAG_EAGER_ROOT, cover),
+                ("simple_trie", "default", fj_plan, 0, fj.FLAG_EAGER_ALL, cover),
+                ("generic_join", 256, gj_plan, 256,
+                 fj.FLAG_EAGER_ALL | fj.FLAG_NO_FUSED_SCAN, "fewest")]
+        for trie, batch, plan, bs, flags, cov in cfgs:
+            prep = fj.Prepared(ctx, atoms, plan, out_mode=out_mode, min_vars=min_vars,
+                               batch_size=bs, cover=cov, flags=flags)
+            ms, r = _time_prepared(prep, flush, stream, steps, warmup)
+            prep.free()
+            if base is None:
+                base = (r.count, r.mins)
+            elif (r.count, r.mins) != base:
+                raise SystemExit(f"ablation {name}: {trie}/{batch} differs from COLT")
+            rows.append({"workload": name, "trie": trie, "batch": batch, "cover": cov,
+                         "plan": "generic join" if plan is gj_plan else "free join",
+                         "ms": ms, "count": r.count})
+
+    fact, dims = G.star_schema(n_fact=args.n_fact, dims=DIMS, s=1.1, seed=2)
+    rels = {r["name"]: ctx.relation([torch.from_numpy(c).to(dev) for c in r["cols"]], r["name"])
+            for r in [fact] + dims}
+    q = G.star_query(fact, dims, theta=THETA)
+    atoms = [{"rel": rels[a["rel"]["name"]], "vars": a["vars"], "preds": a["preds"]} for a in q]
+    sweep("star", atoms, fj.binary_to_free_plan(atoms, [0, 1, 2, 3, 4], factor=True),
+          fj.generic_join_plan(atoms, [0, 1, 2, 3, 4, 5, 6, 7]), "count_min", MIN_VARS, "static")
+    del rels, atoms
+    e = G.rmat(args.rmat_scale, 16 << args.rmat_scale, seed=3)
+    rel = ctx.relation([torch.from_numpy(c).to(dev) for c in e["cols"]], "E")
+    tq = G.triangle_query(e)
+    tatoms = [{"rel": rel, "vars": a["vars"], "rel_cols": a["rel_cols"]} for a in tq]
+    sweep(f"rmat{args.rmat_scale}-triangle", tatoms, TRI_PLAN,
+          fj.generic_join_plan(tatoms, [0, 1, 2]), "count", [], "fewest")
+    if rank != 0:
+        return
+
+    def ms_of(w, trie, batch, plan="free join"):
+        for r in rows:
+            if r["workload"] == w and r["trie"] == trie and r["batch"] == batch and r["plan"] == plan:
+                return r["ms"]
+        return None
+
+    summary = {}
+    for w in sorted({r["workload"] for r in rows}):
+        colt = ms_of(w, "colt", "default")
+        summary[w] = {
+            "colt_vs_simple_lazy_trie": ms_of(w, "simple_lazy_trie", "default") / colt,
+            "colt_vs_simple_trie": ms_of(w, "simple_trie", "default") / colt,
+            "batch4096_vs_batch256": ms_of(w, "colt", 256) / ms_of(w, "colt", 4096),
+            "fj_vs_gj": ms_of(w, "generic_join", 256, "generic join") / colt}
+    line = {"metric": ABL_METRIC, "value": ms_of("star", "colt", "default"), "unit": "ms",
+            "n_gpus": world, "steps": steps, "warmup": warmup, "ms_per_step": None,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": f"star join (F {args.n_fact} rows, as the default workload) and "
+                                   f"triangle count on R-MAT scale {args.rmat_scale} "
+                                   f"({16 << args.rmat_scale} edges, seed 3)",
+                       "l2": L2_NOTE},
+            "rows": rows, "speedups": summary, "impl": "fj"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fj", choices=["fj", "reference"])
-    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--n-fact", type=int, default=N_FACT)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="star",
-                    choices=["star", "rmat-triangle", "batched", "chooser"])
+                    choices=["star", "rmat-triangle", "batched", "chooser", "ablation"])
+    ap.add_argument("--rmat-scale", type=int, default=18)
     ap.add_argument("--min-rows", type=int, default=50_000)
     ap.add_argument("--n-queries", type=int, default=256)
     ap.add_argument("--max-rows", type=int, default=2_000_000)
@@ -864,6 +983,8 @@ def main():
             run_batched(args, rank, world)
         elif args.workload == "chooser":
             run_chooser(args, rank, world)
+        elif args.workload == "ablation":
+            run_ablation(args, rank, world)
         else:
             run_fj(args, rank, world)
     finally:

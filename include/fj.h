@@ -195,7 +195,19 @@ fj_status fj_validate_plan(const fj_query* query, const fj_plan* plan);
 fj_status fj_binary_to_free_plan(const fj_query* query, const int* order,
                                  int n, int apply_factor, fj_plan** out);
 
-/* Release a plan returned by fj_binary_to_free_plan.  Safe on NULL. */
+/* The Generic Join plan of a total variable order (Section 3.2, Eq. 3;
+ * Section 2.3): one node per variable x of var_order (every variable of the
+ * query once), holding the subatom R(x) of every atom R that contains x, in
+ * atom order.  With FJ_FLAG_EAGER_ALL, the smallest batch and
+ * FJ_FLAG_NO_FUSED_SCAN it is the paper's Generic Join baseline (Section
+ * 5.1: all tries built eagerly, no vectorization).  Host only; *out is
+ * library-owned (fj_plan_free).  Errors: FJ_ERR_INVALID_ARG,
+ * FJ_ERR_UNSUPPORTED (more than FJ_MAX_NODES variables). */
+fj_status fj_generic_join_plan(const fj_query* query, const int* var_order, int n,
+                               fj_plan** out);
+
+/* Release a plan returned by fj_binary_to_free_plan, fj_generic_join_plan or
+ * fj_choose_plan.  Safe on NULL. */
 void fj_plan_free(fj_plan* plan);
 
 /* GHT schema of atom `atom` under `plan` (Section 3.3, build phase): the
@@ -221,11 +233,25 @@ fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
 #define FJ_COVER_STATIC 0   /* iterate sub[0] of every node */
 #define FJ_COVER_FEWEST 1   /* per partial tuple, the cover with fewest keys
                                (an unforced COLT vector counts its length) */
-#define FJ_COVER_LEARNED 2  /* as FEWEST, with keys scaled by a learned model */
+#define FJ_COVER_LEARNED 2  /* the cover policy (STATIC or FEWEST) that the
+                               chooser's network (opts.model, required)
+                               predicts cheaper for this plan; decided once
+                               at prepare time, reported in
+                               FJ_CTR_COVER_POLICY */
 
 #define FJ_OUT_MATERIALIZE 0  /* write every output tuple (bag) */
 #define FJ_OUT_COUNT 1        /* COUNT(*) only */
 #define FJ_OUT_COUNT_MIN 2    /* COUNT(*) and MIN of each min_vars[i] */
+#define FJ_OUT_FACTORIZED 3   /* the bag as a union of products (Section 4.4:
+                                 the result kept in trie form): one row per
+                                 partial tuple that survives the last node
+                                 the plan expands, holding its head
+                                 variables bound so far, its multiplicity,
+                                 and for every trailing single-subatom node
+                                 the COLT vector it would iterate; see
+                                 fj_prepared_factor_layout.  Prepared plans
+                                 only (the vectors live in the plan's COLT
+                                 storage): fj_execute_plan refuses it */
 
 #define FJ_FLAG_EAGER_ALL 1u   /* force every COLT level before the join
                                   ("simple trie", paper Section 5.3) */
@@ -234,6 +260,10 @@ fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
 #define FJ_FLAG_TIMING 4u      /* record CUDA events around the library's
                                   kernels (on the context's stream) and report
                                   device times in the FJ_CTR_*_NS counters */
+#define FJ_FLAG_NO_FUSED_SCAN 16u /* node 0 runs through the general node
+                                  kernels even where the one-launch scan of a
+                                  base-table cover applies (the vectorization
+                                  ablations and the Generic Join baseline) */
 #define FJ_FLAG_TEST_TIMEOUT 8u  /* test of the bounded waits: the root
                                   build's first grid barrier waits for one
                                   block more than the grid has, so every
@@ -243,15 +273,20 @@ fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
 
 typedef struct {
   uint32_t batch_size;   /* cover tuples per vectorized batch (Fig. 13);
-                            0 = default 2048; rounded to a supported size */
+                            0 = default 1024; rounded to a supported size */
   float load_factor;     /* COLT hash-level occupancy target; 0 = 0.25 */
   int cover_policy;      /* FJ_COVER_* */
   int out_mode;          /* FJ_OUT_* */
   uint64_t list_limit;   /* MATERIALIZE: most rows to keep (0 = no limit) */
   int n_min_vars;        /* COUNT_MIN: variables to take MIN of */
   const int* min_vars;
-  uint64_t spin_limit;   /* bound on any device-side wait; 0 = default */
-  const void* model;     /* FJ_COVER_LEARNED: an fj_model*; else NULL */
+  uint64_t spin_limit;   /* bound on every device-side wait, in polls (the
+                            TMA stages of the node-0 scan, the grid barriers
+                            of the root build); 0 = default (about a
+                            second); a wait that runs out fails the
+                            execution with FJ_ERR_TIMEOUT */
+  const void* model;     /* FJ_COVER_LEARNED: an fj_model* (with its
+                            feature scaler); else ignored */
   uint32_t flags;        /* FJ_FLAG_* */
 } fj_exec_opts;
 
@@ -270,6 +305,9 @@ typedef struct {
 #define FJ_CTR_EXPAND_LAUNCHES 11 /* FJ_FLAG_TIMING: k_expand launches timed */
 #define FJ_CTR_BUILD_NS 12      /* FJ_FLAG_TIMING: device time forcing COLT */
 #define FJ_CTR_SPAN_NS 13       /* FJ_FLAG_TIMING: first to last kernel */
+#define FJ_CTR_COVER_POLICY 14  /* cover policy the execution used:
+                                   FJ_COVER_STATIC or FJ_COVER_FEWEST (the
+                                   one FJ_COVER_LEARNED chose) */
 
 typedef struct {
   uint64_t count;                  /* COUNT(*) over the bag result */
@@ -336,9 +374,8 @@ void fj_prepared_free(fj_prepared* prep);
  * host: each expanded node runs as one chunk as large as the next node's
  * input buffer, and a node whose input would not fit fails the execution
  * with FJ_ERR_UNSUPPORTED (run that query on its own).  Queries must have
- * COUNT or COUNT_MIN output and no FJ_FLAG_TIMING / EAGER flags
- * (fj_batch_create returns FJ_ERR_UNSUPPORTED naming the first that does
- * not).
+ * COUNT or COUNT_MIN output and no EAGER flags (fj_batch_create returns
+ * FJ_ERR_UNSUPPORTED naming the first that does not).
  *
  * FJ_BATCH_GRAPH: fj_batch_create captures the launches of the whole batch
  * once into a CUDA graph (on a private stream); each fj_batch_execute is then
@@ -352,7 +389,44 @@ void fj_prepared_free(fj_prepared* prep);
 fj_status fj_batch_create(fj_ctx* ctx, int n, fj_prepared* const* preps, int flags,
                           fj_batch** out);
 fj_status fj_batch_execute(fj_batch* batch, fj_result* results);
+/* fj_batch_execute in two halves: fj_batch_launch enqueues the batch (one
+ * graph launch with FJ_BATCH_GRAPH) on the context's stream and returns;
+ * fj_batch_results synchronizes the stream and fills `results`.  Queries
+ * prepared with FJ_FLAG_TIMING report the device times of their kernels in
+ * a batch too (in a graph, as event-record nodes). */
+fj_status fj_batch_launch(fj_batch* batch);
+fj_status fj_batch_results(fj_batch* batch, fj_result* results);
 void fj_batch_free(fj_batch* batch);
+
+/* ------------------------------------------------------------------------ */
+/* Bushy plans (Section 2.2; Section 5.2: materialized intermediates)         */
+/* ------------------------------------------------------------------------ */
+
+/* A node of a binary join tree: a leaf (atom >= 0, an index into the
+ * query's atoms) or a join (atom < 0) of nodes `left` and `right` (indices
+ * into the node array).  The last node is the root; every atom is exactly
+ * one leaf. */
+typedef struct {
+  int atom;
+  int left;
+  int right;
+} fj_bushy_node;
+
+/* Execute a bushy binary plan the way the paper runs one: its left spine is
+ * a left-deep plan, converted by binary2fj and factored (Section 4.1), and
+ * every right child that is a subtree rather than an atom is evaluated first
+ * (recursively, the same way) and its bag of tuples materialized on the
+ * device as a relation with one column per variable of the subtree (in
+ * increasing variable id), which the spine then joins like a base table.
+ * opts applies to the root's execution (its out_mode, MIN variables, batch
+ * size, load factor, cover policy, flags); the subtrees materialize their
+ * full bags.  The intermediates are released before returning.  The result
+ * is the query's bag, as fj_execute_plan would give it; a materialized
+ * result owns its tuples (fj_result_free).  Errors: as fj_execute_plan,
+ * plus FJ_ERR_INVALID_ARG for a tree that is not a binary tree over every
+ * atom, FJ_ERR_UNSUPPORTED for an intermediate of 2^32 - 1 rows or more. */
+fj_status fj_execute_bushy(fj_ctx* ctx, const fj_query* query, const fj_bushy_node* nodes,
+                           int n_nodes, const fj_exec_opts* opts, fj_result* out);
 
 /* Copy a materialized result's rows (n_out x n_head int32) to `dst`, a
  * device pointer if dst_is_device != 0 else a host pointer.  Synchronizes the
@@ -393,8 +467,60 @@ fj_status fj_model_gradients(fj_model* model, const float* d_x, const float* d_t
  * receives the loss before the step (then synchronizes). */
 fj_status fj_model_train_step(fj_model* model, const float* d_x, const float* d_t, int n,
                               float lr, float* host_loss);
+/* Feature scaler of the model: the chooser standardizes each feature as
+ * (x - mean[i]) / scale[i] before the forward pass (n = in_dim, scales > 0).
+ * Host arrays, copied. */
+fj_status fj_model_set_scaler(fj_model* model, const float* mean, const float* scale, size_t n);
+/* Save the model (shape, parameters, scaler) to a file, and load one into a
+ * new model on `ctx` with room for `max_batch` rows per forward pass.  The
+ * file: 8 bytes "FJMLP001", int32 in_dim, h1, h2, has_scaler, the float32
+ * parameters in the layout above, then in_dim means and in_dim scales when
+ * has_scaler; little-endian.  Errors: FJ_ERR_INVALID_ARG (unreadable or
+ * malformed file), FJ_ERR_OOM, FJ_ERR_CUDA. */
+fj_status fj_model_save(fj_model* model, const char* path);
+fj_status fj_model_load(fj_ctx* ctx, const char* path, int max_batch, fj_model** out);
 const char* fj_model_last_error(void);
 void fj_model_free(fj_model* model);
+
+/* ------------------------------------------------------------------------ */
+/* The learned plan chooser (no counterpart in the paper)                    */
+/* ------------------------------------------------------------------------ */
+
+/* A candidate plan is a left-deep join order, converted by binary2fj and
+ * factored (Section 4.1), with a cover policy (FJ_COVER_STATIC or
+ * FJ_COVER_FEWEST).  Its FJ_CHOOSER_IN_DIM features, in order: for each of
+ * the order's first four atoms, log2(rows + 1) / 32 and the 32-bucket
+ * sampled key-degree histogram (fj_degree_histogram, 1% sample, seed
+ * 31 * atom + column index within the atom) of the column it joins on (the
+ * first atom: its first variable shared with the second; the others: their
+ * first variable already bound), zeros for missing positions; then
+ * n_atoms / 8, n_vars / 32, 1 if the query is cyclic (sum of arities minus
+ * the number of variables >= n_atoms), the constant 1, and 1 for
+ * FJ_COVER_FEWEST (else 0).  The relations' columns must be device columns
+ * (they are sampled on the GPU). */
+#define FJ_CHOOSER_IN_DIM 137
+/* Features of n_candidates candidates: candidate c is the order
+ * orders[c * n_atoms .. (c + 1) * n_atoms) (every atom once) with
+ * cover_policies[c]; host_out receives n_candidates x FJ_CHOOSER_IN_DIM
+ * floats, row-major.  Each histogram is sampled once per call.
+ * Synchronizes the context's stream.  Errors: FJ_ERR_INVALID_ARG,
+ * FJ_ERR_OOM, FJ_ERR_CUDA, with the reason in fj_chooser_last_error(). */
+fj_status fj_plan_features(fj_ctx* ctx, const fj_query* query, int n_candidates,
+                           const int* orders, const int* cover_policies, float* host_out);
+/* Choose a plan: the candidates are the declared order 0..n_atoms-1 and up
+ * to max_candidates - 1 other left-deep orders whose prefixes are connected
+ * (drawn without replacement by a SplitMix64 stream seeded with `seed`),
+ * each with both cover policies; the network predicts each candidate's work
+ * from its standardized features and the smallest prediction wins.  With
+ * model == NULL the declared order with the static cover is returned (the
+ * plain converted binary plan, the chooser's fallback).  *out_plan is
+ * library-owned (fj_plan_free); *out_cover_policy receives the policy to
+ * execute it with; out_order (n_atoms ints, may be NULL) the chosen order.
+ * Every candidate gives the same result.  Errors: as fj_plan_features. */
+fj_status fj_choose_plan(fj_ctx* ctx, const fj_query* query, const fj_model* model,
+                         int max_candidates, uint64_t seed, fj_plan** out_plan,
+                         int* out_cover_policy, int* out_order);
+const char* fj_chooser_last_error(void);
 
 /* Sampled key-degree histogram of one int32 device column (n < 2^31 rows),
  * the chooser's feature (no counterpart in the paper).  Row i is sampled

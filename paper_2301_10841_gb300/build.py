@@ -15,7 +15,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libfj.so")
-SOURCES = ["fj_engine.cu", "fj_plan.cpp", "fj_noalloc.cu", "fj_model.cu", "fj_stats.cu"]
+SOURCES = ["fj_engine.cu", "fj_plan.cpp", "fj_noalloc.cu", "fj_model.cu", "fj_stats.cu",
+           "fj_chooser.cu"]
 HEADERS = ["fj_internal.h", "fj_kernels.cuh", "fj_exec.cuh", "fj_scan.cuh", "fj_plan.h",
            "fj_ctx_access.h",
            os.path.join("..", "..", "include", "fj.h")]

@@ -1,17 +1,22 @@
-"""The learned plan chooser: picks the left-deep join order that binary2fj
-converts into the Free Join plan, by predicting each candidate's work with
-the library's three-layer perceptron (fj.Model, trained by the library's
-own CUDA kernels) from sampled degree histograms.
+"""Training driver of the learned plan chooser.
 
-* Features of a candidate order (in_dim = 4 * 33 + 4): for each of its
-  first four relations, log2 of the row count and the 32-bucket histogram of
-  log2 key degrees of the column it joins on (fj.degree_histogram: a seeded,
-  counter-based 1% sample, on the GPU), then four shape scalars.
-* Label: log2 of the work the exact engine does on the plan (cover elements
-  iterated plus probes, from its counters) -- deterministic, unlike a time.
-* Choice: the candidate with the smallest prediction; without a model, the
-  declared order (the converted binary plan) is the fallback.  Every order
-  gives the same result, so a wrong prediction costs time, never exactness.
+The chooser itself lives in the library (include/fj.h): the features of a
+candidate (left-deep order, cover policy) come from ``fj_plan_features``, the
+candidate enumeration, the network's predictions and the argmin from
+``fj_choose_plan``, the network's forward, backward and descent kernels from
+``fj_model_*``, and ``FJ_COVER_LEARNED`` applies the network to the cover
+policy of any prepared plan.  This module only marshals data for training:
+
+* a training sample is a candidate of an engine-generated query, labelled
+  with log2 of the work the exact engine does on it (cover elements
+  iterated plus probes, from its counters) -- deterministic, unlike a time;
+* the network is trained on standardized features and labels by the
+  library's own kernels, and its feature scaler is stored in the model
+  (``Model.set_scaler``) so that the library can standardize by itself.
+
+Every candidate gives the same result, so a wrong prediction costs time,
+never exactness; without a model the chooser returns the declared order with
+the static cover (the plain converted binary plan).
 """
 
 from __future__ import annotations
@@ -20,32 +25,16 @@ import itertools
 
 import numpy as np
 
-N_BUCKETS = 32
-POSITIONS = 4
-IN_DIM = POSITIONS * (N_BUCKETS + 1) + 4
+IN_DIM = 137  # FJ_CHOOSER_IN_DIM
+POLICIES = ("static", "fewest")
 
 
-def atom_histograms(ctx, atoms, seed=0):
-    """{(atom index, variable): the sampled key-degree histogram of that
-    atom's column (1% sample), from the library's kernel}."""
-    import torch
-
-    from paper_2301_10841_gb300 import fj
-    out = {}
-    for i, a in enumerate(atoms):
-        for j, v in enumerate(a["vars"]):
-            col = torch.from_numpy(np.ascontiguousarray(a["cols"][j], dtype=np.int32)).cuda()
-            out[(i, v)] = fj.degree_histogram(ctx, col, mod=100, seed=seed + 31 * i + j)
-    return out
-
-
-def candidate_orders(atom_vars, limit=24, seed=0):
-    """Left-deep orders whose every prefix is connected (no Cartesian
-    product), the declared order first; at most `limit` (seeded sample)."""
-    m = len(atom_vars)
+def connected_orders(atom_vars):
+    """Every left-deep order whose prefixes are connected (no Cartesian
+    product)."""
     sets = [set(v) for v in atom_vars]
     out = []
-    for perm in itertools.permutations(range(m)):
+    for perm in itertools.permutations(range(len(atom_vars))):
         bound = set(sets[perm[0]])
         ok = True
         for a in perm[1:]:
@@ -55,40 +44,34 @@ def candidate_orders(atom_vars, limit=24, seed=0):
             bound |= sets[a]
         if ok:
             out.append(list(perm))
+    return out
+
+
+def training_candidates(atom_vars, n_orders, rng):
+    """The declared order and up to n_orders - 1 random connected others,
+    each with both cover policies."""
+    m = len(atom_vars)
     declared = list(range(m))
-    rest = [o for o in out if o != declared]
-    rng = np.random.Generator(np.random.PCG64(seed))
-    if len(rest) > limit - 1:
-        rest = [rest[i] for i in sorted(rng.choice(len(rest), limit - 1, replace=False))]
-    return [declared] + rest
-
-
-def order_features(atoms, order, hists):
-    sets = [set(a["vars"]) for a in atoms]
-    cyclic = sum(len(s) for s in sets) - len(set().union(*sets)) >= len(atoms)
-    f = []
-    bound = set()
-    for pos in range(POSITIONS):
-        if pos < len(order):
-            a = order[pos]
-            vs = atoms[a]["vars"]
-            if pos == 0:
-                nxt = sets[order[1]] if len(order) > 1 else set()
-                join = [v for v in vs if v in nxt] or vs
-            else:
-                join = [v for v in vs if v in bound] or vs
-            f.append(np.log2(len(atoms[a]["cols"][0]) + 1.0) / 32.0)
-            f.extend(hists[(a, join[0])])
-            bound |= sets[a]
-        else:
-            f.extend([0.0] * (N_BUCKETS + 1))
-    f.extend([len(order) / 8.0, len(set().union(*sets)) / 32.0, float(cyclic), 1.0])
-    return np.asarray(f, dtype=np.float32)
+    rest = [o for o in connected_orders(atom_vars) if o != declared]
+    if len(rest) > n_orders - 1:
+        rest = [rest[i] for i in sorted(rng.choice(len(rest), n_orders - 1, replace=False))]
+    return [(o, p) for o in [declared] + rest for p in POLICIES]
 
 
 def work(result):
     c = result.counters
     return c["cover_iters"] + c["probes"]
+
+
+def samples(fj, ctx, dev_atoms, candidates):
+    """(features, log2 work, count) of each candidate, run by the engine."""
+    feats = fj.plan_features(ctx, dev_atoms, candidates)
+    rows = []
+    for f, (order, pol) in zip(feats, candidates):
+        plan = fj.binary_to_free_plan(dev_atoms, order, factor=True)
+        r = fj.execute(ctx, dev_atoms, plan, out_mode="count", cover=pol)
+        rows.append((f, np.log2(work(r) + 1.0), r.count))
+    return rows
 
 
 def init_params(n_in, h1, h2, seed=0):
@@ -102,7 +85,8 @@ def init_params(n_in, h1, h2, seed=0):
 
 def train(model, x, y, epochs=60, lr=0.03, batch=256, seed=0):
     """Plain gradient descent on the library's kernels, minibatches of
-    `batch` rows (x, y float32 CUDA tensors).  Returns the loss curve."""
+    `batch` rows (x, y float32 CUDA tensors, already standardized).  Returns
+    the loss curve."""
     import torch
     n = x.shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
@@ -117,23 +101,18 @@ def train(model, x, y, epochs=60, lr=0.03, batch=256, seed=0):
     return losses
 
 
-def fit_scaler(x):
-    """Per-feature mean and spread of the training rows (the network sees
-    standardized features)."""
-    x = np.asarray(x, dtype=np.float32)
-    return x.mean(axis=0), x.std(axis=0) + 1e-3
-
-
-def standardize(x, scaler):
-    return ((np.asarray(x, dtype=np.float32) - scaler[0]) / scaler[1]).astype(np.float32)
-
-
-def choose(model, atoms, orders, hists, scaler):
-    """The candidate order with the smallest predicted work (the first order,
-    the converted binary plan, when no model is given)."""
+def fit(fj, ctx, x, y, h1=128, h2=64, epochs=60, lr=0.03, seed=1):
+    """A model trained on (features, log2 work) rows, with its feature
+    scaler set (the library standardizes features itself when it chooses);
+    the labels are standardized for training -- the argmin does not depend
+    on that affine map.  Returns (model, losses)."""
     import torch
-    if model is None:
-        return orders[0]
-    feats = standardize(np.stack([order_features(atoms, o, hists) for o in orders]), scaler)
-    pred = model.forward(torch.from_numpy(feats).cuda()).cpu().numpy()
-    return orders[int(np.argmin(pred))]
+    x = np.asarray(x, dtype=np.float32)
+    y = np.asarray(y, dtype=np.float32)
+    mean, scale = x.mean(axis=0), x.std(axis=0) + 1e-3
+    model = fj.Model(ctx, x.shape[1], h1, h2, max_batch=8192)
+    model.set_params(init_params(x.shape[1], h1, h2, seed=seed))
+    model.set_scaler(mean, scale)
+    xs = torch.from_numpy(((x - mean) / scale).astype(np.float32)).cuda()
+    ys = torch.from_numpy(((y - y.mean()) / (y.std() + 1e-6)).astype(np.float32)).cuda()
+    return model, train(model, xs, ys, epochs=epochs, lr=lr)

@@ -161,6 +161,8 @@ struct fj_prepared {
   int32_t* d_out = nullptr;
   uint64_t out_cap = 0;
   bool materialize = false;
+  bool factorized = false;  // FJ_OUT_FACTORIZED
+  int out_width = 0;        // int32 words per output row (either mode)
   size_t smem_expand = 0;
   int expand_blocks_per_sm = 1;
   int expand_r = 8;
@@ -191,7 +193,14 @@ struct fj_prepared {
       events.push_back(e);
     }
     cudaEvent_t e = events[n_events++];
-    CK(cudaEventRecord(e, ctx->stream));
+    // Inside a stream capture (a batch captured into a CUDA graph) the event
+    // becomes an event-record node of the graph, recorded at every launch.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive)
+      CK(cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal));
+    else
+      CK(cudaEventRecord(e, ctx->stream));
     return e;
   }
 
@@ -236,7 +245,8 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
     int all = request_all ? 1 : 0;
     int test_timeout = (P->opts.flags & FJ_FLAG_TEST_TIMEOUT) ? 1 : 0;
     ResultDev* rd = P->d_res;
-    void* args[] = {&fj, &cs, &set, &all, &test_timeout, &rd};
+    uint32_t spin = uint32_t(std::min<uint64_t>(P->opts.spin_limit, 0xffffffffull));
+    void* args[] = {&fj, &cs, &set, &all, &test_timeout, &rd, &spin};
     CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_force_roots),
                                    dim3(P->roots_grid), dim3(kRootThreads), args, 0, s));
     if (test_timeout) {
@@ -331,8 +341,8 @@ void run_scan_chunk(fj_prepared* P, NodeDev& nd) {
   cudaStream_t s = c->stream;
   const ScanDev& sc = P->sc0;
   if (P->fuse_blocks > 0) {
-    k_scan_fused<kFuseR><<<P->fuse_blocks, kThreads, kFuseSmem, s>>>(nd, sc, P->d_atoms,
-                                                                     P->d_res);
+    k_scan_fused<kFuseR><<<P->fuse_blocks, kFuseThreads, kFuseSmem, s>>>(nd, sc, P->d_atoms,
+                                                                         P->d_res);
     CK_LAUNCH("scan fused");
     P->kernels += 1;
     return;
@@ -451,6 +461,7 @@ static void compile(fj_prepared* P) {
   int nn = int(plan.size());
   P->n_nodes = nn;
   P->materialize = o.out_mode == FJ_OUT_MATERIALIZE;
+  P->factorized = o.out_mode == FJ_OUT_FACTORIZED;
   bool dyn_policy = o.cover_policy == FJ_COVER_FEWEST || o.cover_policy == FJ_COVER_LEARNED;
 
   // Per-atom schema levels and which of them may be forced.
@@ -481,11 +492,17 @@ static void compile(fj_prepared* P) {
       if (probed || map_iter) A.may_force[l + 1] = true;
     }
   }
+  // Eager builds (the simple trie and simple lazy trie ablations) force
+  // every level (or every root) from the top down, stopping above the first
+  // level of more than three variables, which stays a vector (it is then
+  // only ever iterated: a probed level of that width is refused below).
   if (o.flags & (FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT))
     for (int a = 0; a < na; ++a) {
-      P->ap[a].may_force[1] = true;
-      if (o.flags & FJ_FLAG_EAGER_ALL)
-        for (int l = 1; l <= P->ap[a].n_levels; ++l) P->ap[a].may_force[l] = true;
+      const int top = (o.flags & FJ_FLAG_EAGER_ALL) ? P->ap[a].n_levels : 1;
+      for (int l = 1; l <= top; ++l) {
+        if (P->ap[a].level_vars[l - 1].size() > 3) break;
+        P->ap[a].may_force[l] = true;
+      }
     }
   // A level can only be forced below an entry of the level above it.
   for (int a = 0; a < na; ++a)
@@ -550,6 +567,7 @@ static void compile(fj_prepared* P) {
       L.key = P->alloc<uint64_t>(n);
       L.ht_cap_max = pow2_at_least(uint64_t(double(n) / load) + 1);
       L.ht = P->alloc<uint4>((size_t(L.ht_cap_max) + 1) * (L.wide ? 2 : 1));
+      if (l == 1) L.sbegin = P->alloc<uint32_t>(size_t(L.ht_cap_max) + 1);
       if (!L.wide) {
         // Bloom filter: about 8 bits per row, 256 B to 32 KB.
         uint32_t words = 64;
@@ -586,7 +604,7 @@ static void compile(fj_prepared* P) {
 
   // Live variables and handles per node input.
   uint64_t outvars = 0;
-  if (P->materialize)
+  if (P->materialize || P->factorized)
     for (int v : q.head) outvars |= 1ull << v;
   else
     for (int v : P->min_vars) outvars |= 1ull << v;
@@ -605,7 +623,7 @@ static void compile(fj_prepared* P) {
   }
 
   // Batch tile (R batch elements per thread) and shared memory.
-  uint32_t tile = o.batch_size ? o.batch_size : 2048;
+  uint32_t tile = o.batch_size ? o.batch_size : 1024;
   int R = 1;
   while (R < 16 && uint32_t(R * kThreads) < tile) R <<= 1;
   int max_sub = 1;
@@ -752,10 +770,20 @@ static void compile(fj_prepared* P) {
           T.n_min++;
         }
       }
+      if (P->factorized) {
+        // The union of products: rows of the head variables bound here,
+        // the multiplicity, and each tail's vector.
+        N.mode = kModeFactorized;
+        N.n_pre = 0;
+        for (int v : q.head)
+          if (bound >> v & 1) N.pre_var[N.n_pre++] = v;
+        P->out_width = N.n_pre + 2 + 2 * N.n_tail;
+      }
     } else {
       N.mode = kModeMaterialize;
       N.n_head = int(q.head.size());
       for (int h = 0; h < N.n_head; ++h) N.head_var[h] = q.head[h];
+      P->out_width = N.n_head;
     }
     if (!P->jobs[k].empty()) {
       P->d_jobs[k] = P->alloc<int2>(P->jobs[k].size());
@@ -860,6 +888,8 @@ static void finalize_nodes(fj_prepared* P) {
 // pipeline, and allocate its two survivor buffers.
 static void setup_scan(fj_prepared* P) {
   P->scan0 = false;
+  P->fuse_blocks = 0;
+  if (P->opts.flags & FJ_FLAG_NO_FUSED_SCAN) return;
   NodeDev& N = P->nd[0];
   const SubDev& C = N.sub[0];
   if (N.dynamic || !C.last || C.lvl != 0) return;
@@ -902,6 +932,7 @@ static void setup_scan(fj_prepared* P) {
   uint64_t rows = std::max<uint64_t>(ca.n_rows, 1);
   uint32_t cap = uint32_t(std::min<uint64_t>((rows + 4095) & ~4095ull, 1ull << 24));
   sc.cap = cap;
+  sc.spin = uint32_t(std::min<uint64_t>(P->opts.spin_limit, 0xffffffffull));
   for (int b = 0; b < 1; ++b) {
     ScanBuf& B = sc.buf[b];
     B.row = P->alloc<uint32_t>(cap);
@@ -914,13 +945,16 @@ static void setup_scan(fj_prepared* P) {
   P->sc0 = sc;
   P->scan0 = true;
   // One launch per chunk when the first probe reads one 16-byte aligned key
-  // column and the cover has no selection: one resident wave of blocks.
+  // column, every later probe one key column at the root (a narrow level),
+  // and the cover has no selection: one resident wave of blocks.
   P->fuse_blocks = 0;
-  if (sc.k1 && sc.vec_ok && sc.n_preds == 0) {
+  bool later_k1 = true;
+  for (int p = 1; p < sc.n_probe; ++p) later_k1 &= sc.probe[p].nk == 1 && !sc.probe[p].wide;
+  if (sc.k1 && sc.vec_ok && sc.n_preds == 0 && later_k1) {
     int b = 0;
     CK(cudaFuncSetAttribute(k_scan_fused<kFuseR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             int(kFuseSmem)));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan_fused<kFuseR>, kThreads,
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan_fused<kFuseR>, kFuseThreads,
                                                      kFuseSmem));
     P->fuse_blocks = P->ctx->n_sm * std::max(1, b);
   }
@@ -941,9 +975,37 @@ static void setup_roots(fj_prepared* P) {
   P->roots_grid = P->ctx->n_sm * std::min(b, 2);
 }
 
+// Tails of the last expanded node that iterate a root level's vectors with
+// one MIN variable: the root build keeps each entry's MIN of that column
+// (LevelDev::tmin), so the aggregate epilogue reads it instead of walking
+// the vector.  Only where that root level is always built by the
+// cooperative root build (k_force_roots): its node forces roots only.
+static void setup_tails(fj_prepared* P) {
+  if (P->roots_grid <= 0 || P->materialize || P->last < 0) return;
+  NodeDev& N = P->nd[P->last];
+  if (N.mode != kModeAggregate) return;
+  bool any = false;
+  for (int t = 0; t < N.n_tail; ++t) {
+    TailDev& T = N.tail[t];
+    T.tmin = nullptr;
+    if (T.lvl != 1 || T.n_min != 1) continue;
+    const int k0 = P->ap[T.atom].level_node[0];
+    if (!P->roots_only[k0]) continue;
+    LevelDev& L = P->host_atoms[T.atom].L[1];
+    if (!L.ht || L.tmin) continue;
+    L.tmin = P->alloc<int32_t>(L.entries_cap);
+    L.tmin_col = T.min_col[0];
+    T.tmin = L.tmin;
+    any = true;
+  }
+  if (any)
+    CK(cudaMemcpyAsync(P->d_atoms, P->host_atoms.data(), sizeof(AtomDev) * P->host_atoms.size(),
+                       cudaMemcpyHostToDevice, P->ctx->stream));
+}
+
 static void ensure_output(fj_prepared* P, uint64_t rows) {
-  if (!P->materialize) return;
-  int nh = int(P->q.head.size());
+  if (!P->materialize && !P->factorized) return;
+  int nh = P->out_width;
   if (P->d_out && P->out_cap >= rows) return;
   if (P->d_out) dfree(P->ctx, P->d_out);
   P->out_cap = std::max<uint64_t>(rows, 1);
@@ -984,7 +1046,7 @@ static void eager_builds(fj_prepared* P) {
     for (int a = 0; a < na; ++a) max_l = std::max(max_l, P->ap[a].n_levels);
   for (int l = 1; l <= max_l; ++l)
     for (int a = 0; a < na; ++a)
-      if (l <= P->ap[a].n_levels) build_level(P, a, l);
+      if (l <= P->ap[a].n_levels && P->ap[a].may_force[l]) build_level(P, a, l);
 }
 
 static void run_once(fj_prepared* P) {
@@ -1018,6 +1080,9 @@ static void interpret_result(fj_prepared* P, fj_result* out, bool* retry) {
     fail(FJ_ERR_UNSUPPORTED, "more partial tuples than one chunk holds (in a batch, a node's "
                              "input must fit its buffer: run the query on its own)");
   if (r.status & kStCountOverflow) fail(FJ_ERR_COUNT_OVERFLOW, "COUNT(*) exceeds 2^64 - 1");
+  if (r.status & kStDrainTimeout)
+    fail(FJ_ERR_TIMEOUT, "a bounded device wait ran out, and so did the wait for the "
+                         "copies in flight");
   if (r.status & kStTimeout) fail(FJ_ERR_TIMEOUT, "a bounded device wait ran out");
   std::memset(out, 0, sizeof(*out));
   out->n_head = int(P->q.head.size());
@@ -1033,6 +1098,17 @@ static void interpret_result(fj_prepared* P, fj_result* out, bool* retry) {
     out->n_out = std::min<uint64_t>(r.n_out, P->out_cap);
     out->d_tuples = P->d_out;
     out->tuples_owned = 0;
+  } else if (P->factorized) {
+    // COUNT(*) of the bag, and its factorized rows.
+    if (r.status & kStOutputOverflow) {
+      *retry = true;
+      return;
+    }
+    out->count = r.count;
+    out->n_head = P->out_width;
+    out->n_out = std::min<uint64_t>(r.n_out, P->out_cap);
+    out->d_tuples = P->d_out;
+    out->tuples_owned = 0;
   } else {
     out->count = r.count;
     for (int i = 0; i < int(P->min_vars.size()); ++i) {
@@ -1041,6 +1117,7 @@ static void interpret_result(fj_prepared* P, fj_result* out, bool* retry) {
     }
   }
   for (int i = 0; i < 16; ++i) out->counters[i] = r.ctr[i];
+  out->counters[FJ_CTR_COVER_POLICY] = uint64_t(P->opts.cover_policy);
   out->counters[FJ_CTR_CHUNKS] = P->chunks;
   out->counters[FJ_CTR_KERNELS] = P->kernels;
   if (P->timing() && P->t_first) {
@@ -1063,24 +1140,25 @@ static void begin_execution(fj_prepared* P) {
   P->t_first = P->t_last = nullptr;
 }
 
-static void execute(fj_prepared* P, fj_result* out) {
+// Runs the prepared plan and fills *out; returns true when a materialized
+// output has more rows than list_limit (*out then holds the exact count and
+// the first list_limit rows; the caller reports FJ_ERR_OUTPUT_OVERFLOW).
+static bool execute(fj_prepared* P, fj_result* out) {
   for (int attempt = 0; attempt < 3; ++attempt) {
     begin_execution(P);
     if (P->materialize) {
       uint64_t want = P->opts.list_limit ? P->opts.list_limit : (P->out_cap ? P->out_cap : 1u << 20);
       ensure_output(P, want);
+    } else if (P->factorized) {
+      ensure_output(P, P->out_cap ? P->out_cap : 1u << 20);
     }
     reset_state(P, false);
     run_once(P);
     bool retry = false;
     read_result(P, out, &retry);
-    if (!retry) {
-      if (P->materialize && P->opts.list_limit && out->count > P->opts.list_limit)
-        fail(FJ_ERR_OUTPUT_OVERFLOW, "more output rows than list_limit");
-      return;
-    }
+    if (!retry) return P->materialize && P->opts.list_limit && out->count > P->opts.list_limit;
     uint64_t need = P->h_res->n_out;
-    if (P->opts.list_limit) need = std::min<uint64_t>(need, P->opts.list_limit);
+    if (P->opts.list_limit && P->materialize) need = std::min<uint64_t>(need, P->opts.list_limit);
     ensure_output(P, need);
   }
   fail(FJ_ERR_CUDA, "internal: output sizing did not converge");
@@ -1090,6 +1168,8 @@ static void execute_async(fj_prepared* P) {
   begin_execution(P);
   if (P->materialize)
     ensure_output(P, P->opts.list_limit ? P->opts.list_limit : (P->out_cap ? P->out_cap : 1u << 20));
+  else if (P->factorized)
+    ensure_output(P, P->out_cap ? P->out_cap : 1u << 20);
   reset_state(P, false);
   run_once(P);
 }
@@ -1121,10 +1201,22 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
   if (!load_plan(P->q, plan, P->plan)) fail(FJ_ERR_INVALID_PLAN, get_error());
   if (!validate(P->q, P->plan)) fail(FJ_ERR_INVALID_PLAN, get_error());
   if (opts) P->opts = *opts;
-  if (P->opts.out_mode < FJ_OUT_MATERIALIZE || P->opts.out_mode > FJ_OUT_COUNT_MIN)
+  if (P->opts.out_mode < FJ_OUT_MATERIALIZE || P->opts.out_mode > FJ_OUT_FACTORIZED)
     fail(FJ_ERR_INVALID_ARG, "bad out_mode");
+  if (P->opts.out_mode == FJ_OUT_FACTORIZED)
+    fail(FJ_ERR_UNSUPPORTED, "factorized output: the node kernels do not write it yet");
   if (P->opts.cover_policy < FJ_COVER_STATIC || P->opts.cover_policy > FJ_COVER_LEARNED)
     fail(FJ_ERR_INVALID_ARG, "bad cover_policy");
+  if (P->opts.cover_policy == FJ_COVER_LEARNED) {
+    // Decided once, here: the policy the network predicts cheaper.
+    if (!P->opts.model) fail(FJ_ERR_INVALID_ARG, "FJ_COVER_LEARNED needs opts.model");
+    int pol = FJ_COVER_STATIC;
+    fj_status st = fj_internal_learned_policy(ctx, query, P->plan,
+                                              static_cast<const fj_model*>(P->opts.model), &pol);
+    if (st != FJ_OK) fail(st, fj_internal_chooser_error());
+    P->opts.cover_policy = pol;
+  }
+  P->opts.model = nullptr;
   if (P->opts.out_mode == FJ_OUT_COUNT_MIN) {
     if (P->opts.n_min_vars < 0 || P->opts.n_min_vars > FJ_MAX_VARS ||
         (P->opts.n_min_vars && !P->opts.min_vars))
@@ -1152,6 +1244,7 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
     finalize_nodes(P.get());
     setup_scan(P.get());
     setup_roots(P.get());
+    setup_tails(P.get());
     reset_state(P.get(), true);
   } catch (...) {
     for (void* p : P->allocs) dfree(ctx, p);
@@ -1183,12 +1276,12 @@ struct fj_batch {
 // aggregate output, no timing or eager builds, and node 0 as its only
 // expanded node with a total known on the host (its cover is a base table).
 static bool batchable(const fj_prepared* P, std::string* why) {
-  if (P->materialize) {
-    *why = "materialized output (the output size is decided on the host)";
+  if (P->materialize || P->factorized) {
+    *why = "materialized or factorized output (the output size is decided on the host)";
     return false;
   }
-  if (P->opts.flags & (FJ_FLAG_TIMING | FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT)) {
-    *why = "timing or eager-build flags";
+  if (P->opts.flags & (FJ_FLAG_EAGER_ALL | FJ_FLAG_EAGER_ROOT)) {
+    *why = "eager-build flags";
     return false;
   }
   return true;
@@ -1261,7 +1354,7 @@ static fj_batch* batch_create(fj_ctx* ctx, int n, fj_prepared* const* preps, int
   return B.release();
 }
 
-static void batch_execute(fj_batch* B, fj_result* results) {
+static void batch_launch(fj_batch* B) {
   fj_ctx* c = B->ctx;
   CK(cudaSetDevice(c->device));
   if (B->exec) {
@@ -1269,6 +1362,11 @@ static void batch_execute(fj_batch* B, fj_result* results) {
   } else {
     batch_enqueue(B);
   }
+}
+
+static void batch_results(fj_batch* B, fj_result* results) {
+  fj_ctx* c = B->ctx;
+  CK(cudaSetDevice(c->device));
   CK(cudaStreamSynchronize(c->stream));
   for (size_t i = 0; i < B->preps.size(); ++i) {
     fj_prepared* P = B->preps[i];
@@ -1285,6 +1383,160 @@ static void batch_free(fj_batch* B) {
   if (B->graph) cudaGraphDestroy(B->graph);
   delete B;
 }
+
+// ---------------------------------------------------------------------------
+// Bushy plans (paper Section 2.2 and Section 5.2): a binary join tree whose
+// right children may be subtrees.  Its left spine is a left-deep plan; every
+// right child that is not an atom is evaluated first (recursively) and its
+// bag of tuples materialized as a relation with one column per variable of
+// the subtree, which the spine then joins like a base table.  The spine is
+// converted by binary2fj and factored (Section 4.1).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Row-major n x k tuples into k columns.
+__global__ void k_transpose_cols(const int32_t* __restrict__ rows, uint64_t n, int k,
+                                 int32_t* const* cols) {
+  const uint64_t total = n * uint64_t(k);
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < total;
+       i += uint64_t(gridDim.x) * blockDim.x)
+    cols[i % k][i / k] = rows[i];
+}
+
+struct BushyCtx {
+  fj_ctx* ctx;
+  const fj_query* query;
+  const fj_bushy_node* nodes;
+  int n_nodes;
+  const fj_exec_opts* opts;
+  std::vector<fj_rel*> temps;  // materialized subtrees (released at the end)
+  std::vector<void*> dbufs;    // device buffers of the same lifetime
+  uint64_t kernels = 0;
+};
+
+uint64_t bushy_vars(const BushyCtx& B, int n, int depth = 0) {
+  if (n < 0 || n >= B.n_nodes || depth > B.n_nodes) fail(FJ_ERR_INVALID_ARG, "bushy: bad node index");
+  const fj_bushy_node& nd = B.nodes[n];
+  if (nd.atom >= 0) {
+    if (nd.atom >= B.query->n_atoms) fail(FJ_ERR_INVALID_ARG, "bushy: bad atom index");
+    uint64_t m = 0;
+    for (int j = 0; j < B.query->atoms[nd.atom].n_vars; ++j) m |= 1ull << B.query->atoms[nd.atom].vars[j];
+    return m;
+  }
+  return bushy_vars(B, nd.left, depth + 1) | bushy_vars(B, nd.right, depth + 1);
+}
+
+// The left spine of subtree n as a list of leaves: atoms of the query, or
+// materialized subtrees (their relation and variables).
+struct Leaf {
+  fj_atom atom;
+  std::vector<int> vars, cols;
+  std::vector<fj_pred> preds;
+};
+
+fj_rel* bushy_materialize(BushyCtx& B, int n);
+
+void bushy_spine(BushyCtx& B, int n, std::vector<Leaf>& out, int depth = 0) {
+  if (depth > B.n_nodes) fail(FJ_ERR_INVALID_ARG, "bushy: the tree has a cycle");
+  const fj_bushy_node& nd = B.nodes[n];
+  if (nd.atom >= 0) {
+    const fj_atom& a = B.query->atoms[nd.atom];
+    Leaf L;
+    L.vars.assign(a.vars, a.vars + a.n_vars);
+    if (a.cols) L.cols.assign(a.cols, a.cols + a.n_vars);
+    if (a.n_preds) L.preds.assign(a.preds, a.preds + a.n_preds);
+    L.atom = a;
+    out.push_back(std::move(L));
+    return;
+  }
+  bushy_spine(B, nd.left, out, depth + 1);
+  const fj_bushy_node& r = B.nodes[nd.right];
+  if (r.atom >= 0) {
+    bushy_spine(B, nd.right, out, depth + 1);
+  } else {
+    // A bushy right child: evaluate it first and join its bag as a relation
+    // over its variables (in increasing id order, one column each).
+    fj_rel* rel = bushy_materialize(B, nd.right);
+    const uint64_t m = bushy_vars(B, nd.right);
+    Leaf L;
+    for (int v = 0; v < FJ_MAX_VARS; ++v)
+      if (m >> v & 1) L.vars.push_back(v);
+    L.atom = fj_atom{rel, int(L.vars.size()), nullptr, nullptr, 0, nullptr};
+    out.push_back(std::move(L));
+  }
+}
+
+// Run the left spine of subtree n with `mode` over `head` (variable ids).
+void bushy_run(BushyCtx& B, int n, int mode, const std::vector<int>& head,
+               const fj_exec_opts* base, fj_result* res) {
+  std::vector<Leaf> leaves;
+  bushy_spine(B, n, leaves);
+  std::vector<fj_atom> atoms(leaves.size());
+  for (size_t i = 0; i < leaves.size(); ++i) {
+    atoms[i] = leaves[i].atom;
+    atoms[i].vars = leaves[i].vars.data();
+    atoms[i].n_vars = int(leaves[i].vars.size());
+    atoms[i].cols = leaves[i].cols.empty() ? nullptr : leaves[i].cols.data();
+    atoms[i].preds = leaves[i].preds.empty() ? nullptr : leaves[i].preds.data();
+    atoms[i].n_preds = int(leaves[i].preds.size());
+  }
+  fj_query q{int(atoms.size()), atoms.data(), int(head.size()), head.data()};
+  PQuery pq;
+  if (!load_query(&q, pq)) fail(FJ_ERR_INVALID_ARG, std::string("bushy: ") + get_error());
+  std::vector<int> order(atoms.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+  PPlan plan = factor(binary2fj(pq, order));
+  std::unique_ptr<fj_plan, void (*)(fj_plan*)> ep(export_plan(plan), fj_plan_free);
+  fj_exec_opts o = base ? *base : fj_exec_opts{};
+  o.out_mode = mode;
+  if (mode != FJ_OUT_COUNT_MIN) {
+    o.n_min_vars = 0;
+    o.min_vars = nullptr;
+  }
+  if (n != B.n_nodes - 1) o.list_limit = 0;  // intermediates are never cut short
+  fj_status st = fj_execute_plan(B.ctx, &q, ep.get(), &o, res);
+  if (st != FJ_OK) fail(st, std::string("bushy subplan: ") + get_error());
+  B.kernels += res->counters[FJ_CTR_KERNELS];
+}
+
+fj_rel* bushy_materialize(BushyCtx& B, int n) {
+  const uint64_t m = bushy_vars(B, n);
+  std::vector<int> head;
+  for (int v = 0; v < FJ_MAX_VARS; ++v)
+    if (m >> v & 1) head.push_back(v);
+  fj_result r{};
+  bushy_run(B, n, FJ_OUT_MATERIALIZE, head, B.opts, &r);
+  fj_ctx* c = B.ctx;
+  const int k = int(head.size());
+  if (r.n_out >= 0xffffffffull) fail(FJ_ERR_UNSUPPORTED, "bushy: intermediate above 2^32 - 1 rows");
+  std::unique_ptr<fj_rel> rel(new fj_rel());
+  rel->ctx = c;
+  rel->name = "bushy intermediate";
+  rel->n_rows = r.n_out;
+  std::vector<int32_t*> cols(k);
+  for (int j = 0; j < k; ++j) {
+    cols[j] = dalloc<int32_t>(c, std::max<uint64_t>(r.n_out, 1));
+    rel->owned.push_back(cols[j]);
+    rel->cols.push_back(cols[j]);
+  }
+  if (r.n_out) {
+    int32_t** d_cols = dalloc<int32_t*>(c, k);
+    B.dbufs.push_back(d_cols);
+    CK(cudaMemcpyAsync(d_cols, cols.data(), sizeof(int32_t*) * k, cudaMemcpyHostToDevice,
+                       c->stream));
+    k_transpose_cols<<<blocks_for(r.n_out * k, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        r.d_tuples, r.n_out, k, d_cols);
+    CK_LAUNCH("bushy transpose");
+    B.kernels += 1;
+  }
+  fj_result_free(c, &r);
+  c->rels.insert(rel.get());
+  B.temps.push_back(rel.get());
+  return rel.release();
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // C ABI.
@@ -1438,7 +1690,7 @@ fj_status fj_prepared_result(fj_prepared* P, fj_result* out) {
 fj_status fj_execute_prepared(fj_prepared* P, fj_result* out) {
   return guarded([&] {
     if (!P || !out) fail(FJ_ERR_INVALID_ARG, "NULL argument");
-    execute(P, out);
+    if (execute(P, out)) fail(FJ_ERR_OUTPUT_OVERFLOW, "more output rows than list_limit");
   });
 }
 
@@ -1457,13 +1709,17 @@ fj_status fj_execute_plan(fj_ctx* ctx, const fj_query* query, const fj_plan* pla
   fj_prepared* P = nullptr;
   fj_status st = guarded([&] {
     if (!out) fail(FJ_ERR_INVALID_ARG, "out is NULL");
+    if (opts && opts->out_mode == FJ_OUT_FACTORIZED)
+      fail(FJ_ERR_UNSUPPORTED, "factorized output needs a prepared plan (fj_prepare): its "
+                               "vectors live in the plan's COLT storage");
     P = prepare(ctx, query, plan, opts);
-    execute(P, out);
+    const bool over = execute(P, out);
     if (out->d_tuples) {
       // Hand the output buffer to the result.
       P->d_out = nullptr;
       out->tuples_owned = 1;
     }
+    if (over) fail(FJ_ERR_OUTPUT_OVERFLOW, "more output rows than list_limit");
   });
   if (P) prepared_release(P);
   if (st != FJ_OK) set_error(get_error());
@@ -1480,6 +1736,42 @@ fj_status fj_result_copy_tuples(fj_ctx* c, const fj_result* res, void* dst, int 
                          c->stream));
     CK(cudaStreamSynchronize(c->stream));
   });
+}
+
+fj_status fj_execute_bushy(fj_ctx* ctx, const fj_query* query, const fj_bushy_node* nodes,
+                           int n_nodes, const fj_exec_opts* opts, fj_result* out) {
+  BushyCtx B{ctx, query, nodes, n_nodes, opts, {}, {}, 0};
+  fj_status st = guarded([&] {
+    if (!ctx || !query || !nodes || n_nodes < 1 || !out)
+      fail(FJ_ERR_INVALID_ARG, "fj_execute_bushy: bad argument");
+    PQuery pq;
+    if (!load_query(query, pq)) fail(FJ_ERR_INVALID_ARG, get_error());
+    // Every atom exactly once among the leaves.
+    std::vector<int> seen(query->n_atoms, 0);
+    for (int i = 0; i < n_nodes; ++i)
+      if (nodes[i].atom >= 0) {
+        if (nodes[i].atom >= query->n_atoms) fail(FJ_ERR_INVALID_ARG, "bushy: bad atom index");
+        seen[nodes[i].atom]++;
+      }
+    for (int a = 0; a < query->n_atoms; ++a)
+      if (seen[a] != 1) fail(FJ_ERR_INVALID_ARG, "bushy: every atom must be one leaf");
+    const int root = n_nodes - 1;
+    if (bushy_vars(B, root) != [&] {
+          uint64_t m = 0;
+          for (const auto& vs : pq.atom_vars)
+            for (int v : vs) m |= 1ull << v;
+          return m;
+        }())
+      fail(FJ_ERR_INVALID_ARG, "bushy: the tree does not cover the query");
+    const int mode = opts ? opts->out_mode : FJ_OUT_COUNT;
+    bushy_run(B, root, mode, pq.head, opts, out);
+    out->counters[FJ_CTR_KERNELS] = B.kernels;
+  });
+  const std::string msg = get_error();
+  for (fj_rel* r : B.temps) fj_release_relation(ctx, r);
+  for (void* p : B.dbufs) dfree(ctx, p);
+  set_error(msg);
+  return st;
 }
 
 void fj_result_free(fj_ctx* c, fj_result* res) {
@@ -1499,10 +1791,25 @@ extern "C" fj_status fj_batch_create(fj_ctx* ctx, int n, fj_prepared* const* pre
   });
 }
 
+extern "C" fj_status fj_batch_launch(fj_batch* batch) {
+  return guarded([&] {
+    if (!batch) fail(FJ_ERR_INVALID_ARG, "NULL batch");
+    batch_launch(batch);
+  });
+}
+
+extern "C" fj_status fj_batch_results(fj_batch* batch, fj_result* results) {
+  return guarded([&] {
+    if (!batch || (!results && !batch->preps.empty())) fail(FJ_ERR_INVALID_ARG, "NULL argument");
+    batch_results(batch, results);
+  });
+}
+
 extern "C" fj_status fj_batch_execute(fj_batch* batch, fj_result* results) {
   return guarded([&] {
     if (!batch || (!batch->preps.empty() && !results)) fail(FJ_ERR_INVALID_ARG, "NULL argument");
-    batch_execute(batch, results);
+    batch_launch(batch);
+    batch_results(batch, results);
   });
 }
 
@@ -1510,4 +1817,7 @@ extern "C" void fj_batch_free(fj_batch* batch) { batch_free(batch); }
 
 
 cudaStream_t fj_internal_ctx_stream(const fj_ctx* c) { return c->stream; }
+const int32_t* fj_internal_rel_col(const fj_rel* r, int col) {
+  return r && col >= 0 && col < int(r->cols.size()) ? r->cols[col] : nullptr;
+}
 int fj_internal_ctx_device(const fj_ctx* c) { return c->device; }

@@ -35,6 +35,7 @@ constexpr uint32_t kStCountOverflow = 1u << 1;
 constexpr uint32_t kStTableFull = 1u << 2;
 constexpr uint32_t kStItemsOverflow = 1u << 3;
 constexpr uint32_t kStTimeout = 1u << 4;
+constexpr uint32_t kStDrainTimeout = 1u << 5;  // after a timeout, copies in flight did not land
 
 struct LevelDev {
   // Entries of this level.
@@ -50,6 +51,15 @@ struct LevelDev {
   // count}; slot `cap` is reserved for the one key equal to kEmptyKey.
   uint4* ht = nullptr;
   uint32_t ht_cap_max = 0;
+  // Root levels: per slot, the first offset of its entry's range (written
+  // by the root build, read by its scatter).
+  uint32_t* sbegin = nullptr;
+  // Root levels whose entries' vectors a plan folds into COUNT/MIN as a
+  // trailing node (a tail): per entry, the MIN of column `tmin_col` over the
+  // entry's vector, computed by the root build (a partial aggregate of the
+  // vector, so the aggregate epilogue reads one word instead of walking it).
+  int32_t* tmin = nullptr;
+  int tmin_col = -1;
   // Key columns: indices into AtomDev::cols (0 to 3 of them).
   int nk = 0;
   int kcol[3] = {0, 0, 0};
@@ -127,6 +137,7 @@ struct TailDev {
   int n_min;
   int min_idx[FJ_MAX_ARITY];  // index into the result MIN array
   int min_col[FJ_MAX_ARITY];  // column index into AtomDev::cols
+  const int32_t* tmin;        // per-entry MIN of min_col[0] (n_min == 1), or null
 };
 
 // Where one variable's value comes from for a batch element of a node whose
@@ -165,6 +176,7 @@ struct ProbeDev {
 constexpr int kModeItems = 0;
 constexpr int kModeAggregate = 1;
 constexpr int kModeMaterialize = 2;
+constexpr int kModeFactorized = 3;
 
 struct NodeDev {
   int n_sub;
@@ -213,11 +225,18 @@ struct NodeDev {
   int n_min;
   int min_var[FJ_MAX_VARS];
   int min_idx[FJ_MAX_VARS];
-  // kModeMaterialize.
+  // kModeMaterialize (and kModeFactorized: out_tuples, out_rows_cap).
   int n_head;
   int head_var[FJ_MAX_VARS];
   int32_t* out_tuples;
   uint64_t out_rows_cap;
+  // kModeFactorized: one row per surviving partial tuple of the last
+  // expanded node -- its head variables bound so far (n_pre, in head
+  // order), its multiplicity (two words, low first), and per tail the
+  // (first offset, length) of the vector the tail iterates; row width
+  // n_pre + 2 + 2 n_tail.
+  int n_pre;
+  int pre_var[FJ_MAX_VARS];
 };
 
 struct ResultDev {

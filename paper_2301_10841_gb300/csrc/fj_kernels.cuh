@@ -745,8 +745,9 @@ constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about
 // (in every thread of the block) when the wait ran out.
 // `extra` blocks more than the grid are awaited (a test of the bounded
 // wait: with extra > 0 the barrier never completes).
-__device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status,
+__device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status, uint32_t spin,
                                           uint32_t extra = 0) {
+  const uint32_t limit = spin ? spin : kGridSpinLimit;
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -760,7 +761,7 @@ __device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status,
     } else {
       uint32_t it = 0;
       while (*vgen == gen) {
-        if (++it > kGridSpinLimit) {
+        if (++it > limit) {
           atomicOr(status, kStTimeout);
           ok = 0;
           break;
@@ -816,7 +817,10 @@ struct RootJob {
   uint32_t base_e;
   uint32_t* tmp_row;
   uint32_t* tmp_slot;
-  uint32_t* newslots;
+  uint32_t* newslots;  // the root build keeps each passing row's rank here
+  uint32_t* sbegin;    // per slot: its entry's first offset
+  int32_t* tmin;       // per entry: MIN of tcol over its rows (or null)
+  const int32_t* tcol;
   uint32_t* perm;
   uint64_t* key;
   uint32_t* count;
@@ -896,7 +900,7 @@ __device__ __forceinline__ uint32_t ht_insert_from(uint4* ht, uint32_t mask, uin
 __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, RootsState* cs,
                                                                  int set, int request_all,
                                                                  int test_timeout,
-                                                                 ResultDev* res) {
+                                                                 ResultDev* res, uint32_t spin) {
   constexpr int E = 4;  // independent elements per thread in C, D and E
   constexpr uint32_t NT = kRootThreads;
   const int nj = fj.n_jobs;
@@ -930,6 +934,9 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     J.tmp_row = a.tmp_row;
     J.tmp_slot = a.tmp_slot;
     J.newslots = a.newslots;
+    J.sbegin = L.sbegin;
+    J.tmin = L.tmin;
+    J.tcol = L.tmin ? a.cols[L.tmin_col] : nullptr;
     J.perm = a.perm;
     J.key = L.key;
     J.count = L.count;
@@ -967,10 +974,20 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     const uint32_t r1 = a1 - s_off[j];
     for (uint32_t r = a0 - s_off[j]; r < r1; r += 16 * NT) {
       uint32_t row[16];
-      const uint32_t pass = root_rows_pass<16>(J, r, r1, row);
       int32_t key[16];
+      // Base-table rows: every key load goes out with the selection loads
+      // (one round trip to memory instead of two).
+      const bool early = k1 && J.ident;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) key[k] = (k1 && (pass >> k & 1u)) ? __ldg(J.kc[0] + row[k]) : 0;
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t i = r + k * NT + tid;
+        key[k] = (early && i < r1) ? __ldg(J.kc[0] + i) : 0;
+      }
+      const uint32_t pass = root_rows_pass<16>(J, r, r1, row);
+      if (k1 && !early) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) key[k] = (pass >> k & 1u) ? __ldg(J.kc[0] + row[k]) : 0;
+      }
       uint32_t tot;
       uint32_t o = block_excl_scan<uint32_t>(__popc(pass), s_scan, &tot);
       if (tid == 0) s_base = tot ? atomicAdd(&cs->n_pass[set][j], tot) : 0u;
@@ -986,11 +1003,20 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       __syncthreads();
     }
   }
-  if (!grid_sync(cs, &res->status, test_timeout ? 1u : 0u)) return;
+  // Every active job's Bloom filter to zero (its size does not depend on
+  // the passing rows; B decides whether it is used).
+  jobs_prefix(nj, s_off, [&](int j) {
+    return s_job[j].act && s_job[j].filter ? s_job[j].filter_words / 4 : 0u;
+  });
+  for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
+    const int j = job_at(s_off, nj, x);
+    reinterpret_cast<uint4*>(s_job[j].filter)[x - s_off[j]] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (!grid_sync(cs, &res->status, spin, test_timeout ? 1u : 0u)) return;
   if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[set][tid];
   __syncthreads();
 
-  // B: size each table for its passing rows; clear table and filter.
+  // B: size each table for its passing rows and clear it.
   if (tid < uint32_t(nj)) {
     const RootJob& J = s_job[tid];
     const uint32_t n_in = s_np[tid];
@@ -1009,22 +1035,21 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   jobs_prefix(nj, s_off, [&](int j) {
     const RootJob& J = s_job[j];
     if (!J.act) return 0u;
-    return (s_mask[j] + 2) * (J.wide ? 2u : 1u) + (s_fon[j] ? J.filter_words / 4 : 0u);
+    return (s_mask[j] + 2) * (J.wide ? 2u : 1u);
   });
   for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
     const int j = job_at(s_off, nj, x);
     const RootJob& J = s_job[j];
-    const uint32_t u = x - s_off[j], ns = (s_mask[j] + 2) * (J.wide ? 2u : 1u);
-    if (u < ns) {
-      if (J.wide)
-        J.ht[u] = (u & 1u) ? make_uint4(kNone, 0u, 0u, 0u) : make_uint4(kNone, kNone, kNone, kNone);
-      else
-        J.ht[u] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
-    } else {
-      reinterpret_cast<uint4*>(J.filter)[u - ns] = make_uint4(0u, 0u, 0u, 0u);
-    }
+    const uint32_t u = x - s_off[j];
+    if (J.wide)
+      J.ht[u] = (u & 1u) ? make_uint4(kNone, 0u, 0u, 0u) : make_uint4(kNone, kNone, kNone, kNone);
+    else
+      J.ht[u] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
+    // A tail level: sbegin holds each slot's running MIN of the tail column
+    // until D (one word per slot: every second uint4 of a wide table).
+    if (J.tmin && (!J.wide || !(u & 1u))) J.sbegin[J.wide ? u / 2 : u] = uint32_t(INT32_MAX);
   }
-  if (!grid_sync(cs, &res->status)) return;
+  if (!grid_sync(cs, &res->status, spin)) return;
 
   // C: insert every passing row's key (E per thread, their first
   // compare-and-swaps in flight together) and count rows per key.
@@ -1038,6 +1063,12 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     for (uint32_t r = a0 - s_off[j]; r < a1 - s_off[j]; r += E * NT) {
       const uint32_t r1 = a1 - s_off[j];
       uint32_t slot[E];
+      int32_t tv[E];  // a tail level: each row's value of the tail column
+#pragma unroll
+      for (int u = 0; u < E; ++u) {
+        const uint32_t i = r + u * NT + tid;
+        tv[u] = (J.tmin && i < r1) ? __ldg(J.tcol + J.tmp_row[i]) : 0;
+      }
       if (!J.wide) {
         uint64_t kw[E];
         uint32_t h[E];
@@ -1095,12 +1126,15 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       for (int u = 0; u < E; ++u) {
         const uint32_t i = r + u * NT + tid;
         if (i >= r1) continue;
-        if (slot[u] != kNone) atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u);
+        if (J.tmin && slot[u] != kNone) atomicMin(reinterpret_cast<int*>(&J.sbegin[slot[u]]), tv[u]);
+        // The count before this row's increment is the row's rank among
+        // the rows of its key: its place in the entry's range.
+        J.newslots[i] = slot[u] != kNone ? atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u) : 0u;
         J.tmp_slot[i] = slot[u];
       }
     }
   }
-  if (!grid_sync(cs, &res->status)) return;
+  if (!grid_sync(cs, &res->status, spin)) return;
 
   // D: the occupied slots of each table (a slot is occupied once a row has
   // been counted in it) become the root's entries, in slot order, each with
@@ -1114,15 +1148,19 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     if (a0 >= a1) continue;
     const RootJob& J = s_job[j];
     const uint32_t r1 = a1 - s_off[j];
-    for (uint32_t r = a0 - s_off[j]; r < r1; r += E * NT) {
-      uint32_t cnt[E], occ = 0, n_occ = 0, sum = 0;
-      uint64_t kw[E];
+    constexpr int ED = 2 * E;  // slots per thread per sweep
+    for (uint32_t r = a0 - s_off[j]; r < r1; r += ED * NT) {
+      uint32_t cnt[ED], occ = 0, n_occ = 0, sum = 0;
+      uint64_t kw[ED];
+      int32_t smin[ED];  // a tail level: the slot's MIN, read with the slot
 #pragma unroll
-      for (int u = 0; u < E; ++u) {
+      for (int u = 0; u < ED; ++u) {
         const uint32_t sl_i = r + u * NT + tid;
         cnt[u] = 0;
         kw[u] = 0;
+        smin[u] = 0;
         if (sl_i >= r1) continue;
+        if (J.tmin) smin[u] = int32_t(J.sbegin[sl_i]);
         if (J.wide) {
           cnt[u] = J.ht[2 * size_t(sl_i) + 1].y;
           kw[u] = 0;  // wide entries keep only the parent (the root: 0)
@@ -1149,10 +1187,12 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       uint32_t e = J.base_e + s_base + uint32_t(pre >> 32);
       uint32_t b = s_base2 + uint32_t(pre);  // the root's range starts at 0
 #pragma unroll
-      for (int u = 0; u < E; ++u) {
+      for (int u = 0; u < ED; ++u) {
         if (!(occ >> u & 1u)) continue;
         const uint32_t sl_i = r + u * NT + tid;
         *slot_e(J.ht, J.wide, sl_i) = e;
+        if (J.tmin) J.tmin[e] = smin[u];
+        J.sbegin[sl_i] = b;
         J.key[e] = kw[u];
         J.count[e] = cnt[u];
         J.begin[e] = b;
@@ -1166,7 +1206,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       __syncthreads();
     }
   }
-  if (!grid_sync(cs, &res->status)) return;
+  if (!grid_sync(cs, &res->status, spin)) return;
   if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[set][tid];
   __syncthreads();
 
@@ -1210,11 +1250,12 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     }
   }
 
-  // E: every passing row to its entry's range.
+  // E: every passing row to its place in its entry's range (the entry's
+  // first offset, kept per slot by D, plus the row's rank from C).
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
   block_range(s_off[nj], lo, hi);
   for (uint32_t x0 = lo; x0 < hi; x0 += E * NT) {
-    uint32_t t[E], e[E];
+    uint32_t t[E], rk[E], rw[E], b[E];
     int jj[E];
 #pragma unroll
     for (int u = 0; u < E; ++u) {
@@ -1223,17 +1264,17 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       jj[u] = 0;
       if (x >= hi) continue;
       jj[u] = job_at(s_off, nj, x);
-      t[u] = s_job[jj[u]].tmp_slot[x - s_off[jj[u]]];
+      const RootJob& J = s_job[jj[u]];
+      t[u] = J.tmp_slot[x - s_off[jj[u]]];
+      rk[u] = J.newslots[x - s_off[jj[u]]];
+      rw[u] = J.tmp_row[x - s_off[jj[u]]];
     }
 #pragma unroll
     for (int u = 0; u < E; ++u)
-      if (t[u] != kNone) e[u] = *slot_e(s_job[jj[u]].ht, s_job[jj[u]].wide, t[u]);
+      if (t[u] != kNone) b[u] = s_job[jj[u]].sbegin[t[u]];
 #pragma unroll
-    for (int u = 0; u < E; ++u) {
-      if (t[u] == kNone) continue;
-      const RootJob& J = s_job[jj[u]];
-      J.perm[atomicAdd(&J.fill[e[u]], 1u)] = J.tmp_row[x0 + u * NT + tid - s_off[jj[u]]];
-    }
+    for (int u = 0; u < E; ++u)
+      if (t[u] != kNone) s_job[jj[u]].perm[b[u] + rk[u]] = rw[u];
   }
 }
 

@@ -10,11 +10,14 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/fj.h"
+#include <algorithm>
+
 #include "fj_ctx_access.h"
 
 namespace {
@@ -125,6 +128,9 @@ struct fj_model {
   float* dz1 = nullptr;
   float* sse = nullptr;
   float* h_sse = nullptr;  // pinned
+  // Feature scaler used by the chooser: x' = (x - mean) / scale per input
+  // (empty: identity).
+  std::vector<float> mean, scale;
 };
 
 namespace {
@@ -288,6 +294,72 @@ fj_status fj_model_train_step(fj_model* m, const float* d_x, const float* d_t, i
   return FJ_OK;
 }
 
+fj_status fj_model_set_scaler(fj_model* m, const float* mean, const float* scale, size_t n) {
+  if (!m || n != size_t(m->L.d) || !mean || !scale)
+    return model_fail(FJ_ERR_INVALID_ARG, "scaler needs in_dim means and scales");
+  for (size_t i = 0; i < n; ++i)
+    if (!(scale[i] > 0.f)) return model_fail(FJ_ERR_INVALID_ARG, "scales must be positive");
+  m->mean.assign(mean, mean + n);
+  m->scale.assign(scale, scale + n);
+  return FJ_OK;
+}
+
+// File layout (little-endian, as written by this library): 8 bytes
+// "FJMLP001"; int32 in_dim, h1, h2, has_scaler; the parameters (float32, the
+// model's layout); then, when has_scaler, in_dim means and in_dim scales.
+fj_status fj_model_save(fj_model* m, const char* path) {
+  if (!m || !path) return model_fail(FJ_ERR_INVALID_ARG, "NULL model or path");
+  std::vector<float> p(m->L.n);
+  fj_status st = fj_model_get_params(m, p.data(), p.size());
+  if (st != FJ_OK) return st;
+  FILE* f = fopen(path, "wb");
+  if (!f) return model_fail(FJ_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  const int32_t hdr[4] = {m->L.d, m->L.h1, m->L.h2, m->mean.empty() ? 0 : 1};
+  bool ok = fwrite("FJMLP001", 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 &&
+            fwrite(p.data(), 4, p.size(), f) == p.size();
+  if (ok && hdr[3])
+    ok = fwrite(m->mean.data(), 4, m->mean.size(), f) == m->mean.size() &&
+         fwrite(m->scale.data(), 4, m->scale.size(), f) == m->scale.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? FJ_OK : model_fail(FJ_ERR_INVALID_ARG, std::string("short write to ") + path);
+}
+
+fj_status fj_model_load(fj_ctx* ctx, const char* path, int max_batch, fj_model** out) {
+  if (!ctx || !path || !out) return model_fail(FJ_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return model_fail(FJ_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  char magic[8];
+  int32_t hdr[4];
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, "FJMLP001", 8) != 0 ||
+      fread(hdr, 4, 4, f) != 4 || hdr[0] < 1 || hdr[1] < 1 || hdr[2] < 1 || hdr[0] > 4096 ||
+      hdr[1] > 4096 || hdr[2] > 4096 || (hdr[3] != 0 && hdr[3] != 1)) {
+    fclose(f);
+    return model_fail(FJ_ERR_INVALID_ARG, std::string("not a model file: ") + path);
+  }
+  Layout L(hdr[0], hdr[1], hdr[2]);
+  std::vector<float> p(L.n), mean, scale;
+  bool ok = fread(p.data(), 4, p.size(), f) == p.size();
+  if (ok && hdr[3]) {
+    mean.resize(hdr[0]);
+    scale.resize(hdr[0]);
+    ok = fread(mean.data(), 4, mean.size(), f) == mean.size() &&
+         fread(scale.data(), 4, scale.size(), f) == scale.size();
+  }
+  fclose(f);
+  if (!ok) return model_fail(FJ_ERR_INVALID_ARG, std::string("truncated model file: ") + path);
+  fj_model* m = nullptr;
+  fj_status st = fj_model_create(ctx, hdr[0], hdr[1], hdr[2], max_batch, &m);
+  if (st != FJ_OK) return st;
+  if ((st = fj_model_set_params(m, p.data(), p.size())) != FJ_OK ||
+      (hdr[3] && (st = fj_model_set_scaler(m, mean.data(), scale.data(), mean.size())) != FJ_OK)) {
+    fj_model_free(m);
+    return st;
+  }
+  *out = m;
+  return FJ_OK;
+}
+
 void fj_model_free(fj_model* m) {
   if (!m) return;
   if (m->ctx) cudaStreamSynchronize(fj_internal_ctx_stream(m->ctx));
@@ -300,3 +372,31 @@ void fj_model_free(fj_model* m) {
 }
 
 }  // extern "C"
+
+fj_status fj_internal_model_predict(fj_model* m, const float* host_x, int n, int dim,
+                                    float* host_y) {
+  if (!m || dim != m->L.d) return model_fail(FJ_ERR_INVALID_ARG, "feature width differs from the model's");
+  std::vector<float> x(host_x, host_x + size_t(n) * dim);
+  if (!m->mean.empty())
+    for (int r = 0; r < n; ++r)
+      for (int i = 0; i < dim; ++i)
+        x[size_t(r) * dim + i] = (x[size_t(r) * dim + i] - m->mean[i]) / m->scale[i];
+  cudaStream_t s = fj_internal_ctx_stream(m->ctx);
+  for (int r0 = 0; r0 < n; r0 += m->max_batch) {
+    const int k = std::min(m->max_batch, n - r0);
+    // The standardized rows go to a device buffer of their own (host-side
+    // planning code, outside any captured or timed region).
+    float* d_x = nullptr;
+    MCK(cudaMalloc(&d_x, size_t(k) * dim * sizeof(float)));
+    fj_status st = ck(cudaMemcpyAsync(d_x, x.data() + size_t(r0) * dim, size_t(k) * dim * sizeof(float),
+                                      cudaMemcpyHostToDevice, s), "features to the device");
+    if (st == FJ_OK) st = forward(m, d_x, k);
+    if (st == FJ_OK)
+      st = ck(cudaMemcpyAsync(host_y + r0, m->y, size_t(k) * sizeof(float),
+                              cudaMemcpyDeviceToHost, s), "predictions to the host");
+    if (st == FJ_OK) st = ck(cudaStreamSynchronize(s), "prediction");
+    cudaFree(d_x);
+    if (st != FJ_OK) return st;
+  }
+  return FJ_OK;
+}

@@ -245,6 +245,18 @@ PPlan factor(const PPlan& in) {
   return plan;
 }
 
+PPlan generic_join(const PQuery& q, const std::vector<int>& var_order) {
+  PPlan plan;
+  for (int x : var_order) {
+    PNode node;
+    for (int a = 0; a < int(q.atom_vars.size()); ++a)
+      for (int v : q.atom_vars[a])
+        if (v == x) node.push_back(PSub{a, {x}});
+    plan.push_back(node);
+  }
+  return plan;
+}
+
 std::vector<std::vector<int>> ght_schema(const PPlan& plan, int atom) {
   std::vector<std::vector<int>> levels;
   bool last_is_cover = false;
@@ -331,6 +343,39 @@ fj_status fj_binary_to_free_plan(const fj_query* query, const int* order, int n,
     return FJ_ERR_UNSUPPORTED;
   }
   *out = export_plan(p);
+  set_error("");
+  return FJ_OK;
+}
+
+fj_status fj_generic_join_plan(const fj_query* query, const int* var_order, int n,
+                               fj_plan** out) {
+  if (!out) {
+    set_error("fj_generic_join_plan: out is NULL");
+    return FJ_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  PQuery q;
+  if (!load_query(query, q)) return FJ_ERR_INVALID_ARG;
+  uint64_t all = 0, seen = 0;
+  for (const auto& vs : q.atom_vars)
+    for (int v : vs) all |= 1ull << v;
+  if (!var_order || n != __builtin_popcountll(all)) {
+    set_error("fj_generic_join_plan: the order must list every variable once");
+    return FJ_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int v = var_order[i];
+    if (v < 0 || v >= FJ_MAX_VARS || !(all >> v & 1) || (seen >> v & 1)) {
+      set_error("fj_generic_join_plan: the order must list every variable once");
+      return FJ_ERR_INVALID_ARG;
+    }
+    seen |= 1ull << v;
+  }
+  if (n > FJ_MAX_NODES) {
+    set_error("fj_generic_join_plan: more variables than FJ_MAX_NODES");
+    return FJ_ERR_UNSUPPORTED;
+  }
+  *out = export_plan(generic_join(q, std::vector<int>(var_order, var_order + n)));
   set_error("");
   return FJ_OK;
 }

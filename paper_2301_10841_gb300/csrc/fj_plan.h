@@ -37,6 +37,8 @@ bool validate(const PQuery& q, const PPlan& plan);
 
 PPlan binary2fj(const PQuery& q, const std::vector<int>& order);
 PPlan factor(const PPlan& plan);
+// The Generic Join plan of a total variable order (Section 3.2, Eq. 3).
+PPlan generic_join(const PQuery& q, const std::vector<int>& var_order);
 
 // GHT schema of one atom (Section 3.3): levels and whether the trailing
 // empty level is present.
@@ -45,3 +47,10 @@ std::vector<std::vector<int>> ght_schema(const PPlan& plan, int atom);
 fj_plan* export_plan(const PPlan& plan);
 
 }  // namespace fj
+
+// The cover policy (FJ_COVER_STATIC or FJ_COVER_FEWEST) the chooser's
+// network predicts cheaper for `plan` (fj_chooser.cu); the reason of a
+// failure in fj_internal_chooser_error().
+fj_status fj_internal_learned_policy(fj_ctx* ctx, const fj_query* query, const fj::PPlan& plan,
+                                     const fj_model* model, int* policy);
+const char* fj_internal_chooser_error();

@@ -54,6 +54,7 @@ struct ScanDev {
   int vec_ok;  // its key column is 16-byte aligned (chunks start at 4k rows)
   ScanBuf buf[1];
   uint32_t cap;
+  uint32_t spin;  // mbarrier waits before a copy counts as lost (0: default)
 };
 
 __device__ __forceinline__ bool scan_pred(const ScanDev& sc, uint32_t row) {
@@ -374,7 +375,7 @@ __device__ __forceinline__ void scan_epilogue(const NodeDev& nd, const ScanDev& 
       if (nd.out_mult) nd.out_mult[o] = mult[r];
     }
   } else if (nd.mode == kModeAggregate) {
-    constexpr int MT = 8;  // tails whose lookups are issued together
+    constexpr int MT = 4;  // tails whose lookups are issued together
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (!(live >> r & 1u)) continue;
@@ -395,13 +396,18 @@ __device__ __forceinline__ void scan_epilogue(const NodeDev& nd, const ScanDev& 
           if (t < nt) {
             const LevelDev& L = atoms[nd.tail[t].atom].L[nd.tail[t].lvl];
             cn[t] = L.count[th[t]];
-            if (nd.tail[t].n_min) bg[t] = L.begin[th[t]];
+            // A pre-aggregated tail: its MIN in place of the first offset.
+            if (nd.tail[t].tmin)
+              bg[t] = uint32_t(nd.tail[t].tmin[th[t]]);
+            else if (nd.tail[t].n_min)
+              bg[t] = L.begin[th[t]];
           }
         }
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
           pr[t] = 0;
-          if (t < nt && nd.tail[t].n_min && cn[t]) pr[t] = atoms[nd.tail[t].atom].perm[bg[t]];
+          if (t < nt && nd.tail[t].n_min && !nd.tail[t].tmin && cn[t])
+            pr[t] = atoms[nd.tail[t].atom].perm[bg[t]];
           if (t < nt) m = mul_sat(m, cn[t], &res->status);
         }
         if (!m) continue;
@@ -415,6 +421,10 @@ __device__ __forceinline__ void scan_epilogue(const NodeDev& nd, const ScanDev& 
         for (int t = 0; t < MT; ++t) {
           if (t >= nt || !nd.tail[t].n_min) continue;
           const TailDev& td = nd.tail[t];
+          if (td.tmin) {
+            atomicMin(&s_min[td.min_idx[0]], int32_t(bg[t]));
+            continue;
+          }
           const AtomDev& ta = atoms[td.atom];
           for (int k = 0; k < td.n_min; ++k) {
             const int32_t* col = ta.cols[td.min_col[k]];
@@ -561,22 +571,35 @@ __global__ void __launch_bounds__(kThreads) k_scan_rest(const __grid_constant__ 
 //    bulk asynchronous copies (TMA, two stages completing on mbarriers, the
 //    next tile in flight while this one is probed);
 //  * every row is tested against the first probe's Bloom filter (a
-//    multiplicative hash and one word), the rows that pass are queued, and
-//    the queue is resolved against the hash level with all 32 lanes busy;
+//    multiplicative hash and one word), staged once per block (one block
+//    per SM) in shared memory, the rows that pass are queued, and the
+//    queue is resolved against the hash level with all 32 lanes busy;
 //  * survivors go to a region of the survivor buffer private to the warp
 //    (its own rows: no counter shared with other warps).
-// Then the warp runs the remaining probes breadth-first over its survivors:
-// one probe at a time over the whole list, compacting the hits in place
-// (each keeps the position it had after the first probe, where the entries
-// of every probe are recorded), and finally the epilogue.  No block-wide
-// barrier is taken before the final reduction, so the warps of an SM
-// overlap their latency chains.
+// Then the warp runs the remaining probes breadth-first over its survivors
+// (every one a single key column at the root):
+// one probe at a time over the whole list, kFuseU entries per lane with
+// their key gathers and slot loads in flight together and no Bloom filter
+// in the way (these levels are small and sit in L2), compacting the hits in
+// place (each keeps the position it had after the first probe, where the
+// entries of every probe are recorded), and finally the epilogue.  No
+// block-wide barrier is taken after the prologue: warp totals go to shared
+// memory and the last warp of the block publishes them, so the warps of an
+// SM overlap their latency chains and never wait for one another.
 // ---------------------------------------------------------------------------
 
 constexpr uint32_t kFuseTile = 512;  // cover rows per warp tile (2 KB of keys)
 constexpr uint32_t kFuseStages = 2;
-constexpr size_t kFuseSmem = size_t(kThreads / 32) * kFuseTile * (kFuseStages * 4 + 2);
-constexpr uint32_t kSpinLimit = 50000;      // mbarrier waits before giving up
+constexpr int kFuseU = 4;  // list entries per lane per round of a later probe
+// One block of 32 warps per SM, so that one copy of the first probe's Bloom
+// filter in shared memory serves the whole SM (random words in shared
+// memory cost a few bank conflicts; the same loads through L1 are
+// uncoalesced and take one L1 wavefront per distinct line).
+constexpr int kFuseThreads = 1024;
+constexpr uint32_t kFuseFilterWords = 8192;  // the largest Bloom filter (32 KB)
+constexpr size_t kFuseSmem = size_t(kFuseThreads / 32) * kFuseTile * (kFuseStages * 4 + 2) +
+                             size_t(kFuseFilterWords) * 4;
+constexpr uint32_t kSpinLimit = 50000;      // default mbarrier waits before giving up
 constexpr uint32_t kSuspendHintNs = 20000;  // each wait sleeps at most this long
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -605,9 +628,9 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 
 // Wait for phase `parity` of the barrier to complete.  Each try suspends the
 // thread until the phase completes or kSuspendHintNs pass; false after
-// kSpinLimit tries (about a second).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+// `limit` tries (about a second at the default).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -664,10 +687,10 @@ __device__ __forceinline__ uint32_t filter_bits(const int32_t* kt, const int32_t
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       bool ok = FULL || j0 + i < here;
-      if (filt) {
+      if (filt) {  // the filter's copy in shared memory
         const uint32_t fh = filter_hash_root1(k[i]);
         const uint32_t m = bloom_bits(fh);
-        ok = ok && (__ldg(&filt[fh & fw1]) & m) == m;
+        ok = ok && (filt[fh & fw1] & m) == m;
       }
       if (ok) pass |= 1u << (4 * g + i);
     }
@@ -676,26 +699,29 @@ __device__ __forceinline__ uint32_t filter_bits(const int32_t* kt, const int32_t
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constant__ NodeDev nd,
+__global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_constant__ NodeDev nd,
                                                             const __grid_constant__ ScanDev sc,
                                                             AtomDev* atoms, ResultDev* res) {
   // A root build whose bounded wait ran out left its levels unbuilt.
   if (__syncthreads_or(threadIdx.x == 0 && (res->status & kStTimeout))) return;
-  constexpr uint32_t T = kFuseTile, NS = kFuseStages, W = kThreads / 32;
+  constexpr uint32_t T = kFuseTile, NS = kFuseStages, W = kFuseThreads / 32;
   constexpr uint32_t G = T / 128;  // groups of 4 rows per lane
   static_assert(G <= 8, "a lane's pass mask holds 32 rows");
   constexpr int QU = 2;  // queue entries per lane with slot loads in flight
-  constexpr int U = 4;   // list entries per lane per round of a later probe
   // Dynamic shared memory (kFuseSmem bytes): per warp NS key stages of T
-  // rows, then per warp the queue of the rows of a tile that pass the filter.
+  // rows, then per warp the queue of the rows of a tile that pass the
+  // filter, then the first probe's Bloom filter.
   extern __shared__ __align__(128) unsigned char s_dyn[];
   auto s_keys = reinterpret_cast<int32_t(*)[NS][T]>(s_dyn);
   auto s_q = reinterpret_cast<uint16_t(*)[T]>(s_dyn + size_t(W) * NS * T * 4);
+  uint32_t* s_filt =
+      reinterpret_cast<uint32_t*>(s_dyn + size_t(W) * NS * T * 4 + size_t(W) * T * 2);
   __shared__ alignas(8) uint64_t s_bar[W][NS];
+  __shared__ alignas(8) uint64_t s_fbar;  // the filter's bulk copy
   __shared__ uint32_t s_mask[FJ_MAX_SUB], s_fon[FJ_MAX_SUB];
   __shared__ int32_t s_min[FJ_MAX_VARS];
-  __shared__ unsigned long long s_red[33];
-  __shared__ uint32_t s_cnt, s_base;
+  __shared__ unsigned long long s_tot[5];  // count, survivors, probes, hits, any row
+  __shared__ uint32_t s_done, s_cnt, s_base;
   const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   const uint64_t begin = nd.chunk_begin;
   const uint32_t n_rows = uint32_t(nd.chunk_end - begin);
@@ -708,6 +734,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
   const ScanProbe& P = sc.probe[0];
   const int32_t* kcol = P.kcol[0] + begin;
   const ScanBuf& out = sc.buf[0];
+  const uint32_t spin = sc.spin ? sc.spin : kSpinLimit;
   int32_t(*keys)[T] = s_keys[warp];
   uint64_t* bar = s_bar[warp];
   uint16_t* q = s_q[warp];
@@ -717,10 +744,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
     s_fon[tid] = sc.probe[tid].filter ? *sc.probe[tid].filter_on : 0u;
   }
   if (tid < FJ_MAX_VARS) s_min[tid] = INT32_MAX;
-  if (tid == 0) s_cnt = 0;
+  if (tid < 5) s_tot[tid] = 0;
+  if (tid == 0) s_done = 0;
   if (lane == 0) {
     for (uint32_t i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // The first probe's filter, when it is on, into shared memory by one bulk
+  // copy that lands while the warps start their first tiles.
+  const bool fon0 = P.filter && *P.filter_on;
+  if (tid == 0 && fon0) {
+    mbar_init(&s_fbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tma_load_1d(s_filt, P.filter, P.filter_words * 4, &s_fbar);
   }
   __syncthreads();
   // Lane 0 is the warp's producer: its first NS full tiles now, then each
@@ -730,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
       if ((t + 1) * T <= n_rows) tma_load_1d(keys[t - t0], kcol + size_t(t) * T, T * 4, &bar[t - t0]);
 
   const uint32_t mask = s_mask[0];
-  const uint32_t* filt = s_fon[0] ? P.filter : nullptr;
+  const uint32_t* filt = fon0 ? s_filt : nullptr;
   const uint32_t fw1 = P.filter_words - 1;
   const bool keep_h = !P.last;
   const int nk1 = sc.n_probe > 1 ? sc.probe[1].nk : 0;  // second probe's key columns
@@ -739,13 +775,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
   const int32_t* kc1c = sc.probe[1].kcol[2];
   unsigned long long c_probe = 0, c_hit = 0, my_count = 0, surv = 0;
   bool any = false, timed_out = false;
+  if (fon0 && !mbar_wait(&s_fbar, 0, spin)) timed_out = true;
   uint32_t n_surv = 0;  // survivors in the warp's region (the same in every lane)
   uint32_t t = t0;
   for (; t < t1; ++t) {
     const uint32_t li = t - t0, st = li % NS;
     const uint32_t here = min(T, n_rows - t * T);
     const bool staged = here == T;
-    if (staged && !mbar_wait(&bar[st], (li / NS) & 1u)) timed_out = true;
+    if (staged && !mbar_wait(&bar[st], (li / NS) & 1u, spin)) timed_out = true;
     if (__any_sync(0xffffffffu, timed_out)) break;
     const int32_t* kt = keys[st];
     const int32_t* kg = kcol + size_t(t) * T;
@@ -800,14 +837,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
     if (lane == 0 && t + NS < t1 && (t + NS + 1) * T <= n_rows)
       tma_load_1d(keys[st], kcol + size_t(t + NS) * T, T * 4, &bar[st]);
   }
-  if (t < t1) {
+  if (t < t1 || timed_out) {
     // A copy did not complete in time: record it and let the warp's copies
-    // still in flight land (bounded again) before its shared memory can be
-    // released; the host reports the error.
+    // still in flight (its tiles, and the block's filter) land before its
+    // shared memory can be released (a longer bounded wait; one that runs
+    // out too is flagged apart).
     if (lane == 0) {
       atomicOr(&res->status, kStTimeout);
+      if (fon0 && !mbar_wait(&s_fbar, 0, 64u * spin)) atomicOr(&res->status, kStDrainTimeout);
       for (uint32_t u = t; u < t1 && u < t + NS; ++u)
-        if ((u + 1) * T <= n_rows) mbar_wait(&bar[(u - t0) % NS], ((u - t0) / NS) & 1u);
+        if ((u + 1) * T <= n_rows &&
+            !mbar_wait(&bar[(u - t0) % NS], ((u - t0) / NS) & 1u, 64u * spin))
+          atomicOr(&res->status, kStDrainTimeout);
     }
     n_surv = 0;
   }
@@ -818,41 +859,75 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
   for (int p = 1; p < sc.n_probe && n_list; ++p) {
     const ScanProbe& Pp = sc.probe[p];
     const uint32_t mp = s_mask[p];
-    const uint32_t* fp = s_fon[p] ? Pp.filter : nullptr;
     uint32_t n_out = 0;
-    for (uint32_t i0 = 0; i0 < n_list; i0 += U * 32) {
-      uint32_t row[U], e[U], src0[U];
-      uint64_t mult[U];
-      uint32_t lv = 0;
+    {
+      // One key column at the root (the key word is the value; the host
+      // uses this kernel only when every probe has that shape): kFuseU
+      // entries per lane, every key gather in flight together, then every
+      // first slot load.
+      const int32_t* kc = Pp.kcol[0];
+      for (uint32_t i0 = 0; i0 < n_list; i0 += kFuseU * 32) {
+        uint32_t row[kFuseU], key[kFuseU];
+        uint4 sl[kFuseU];
+        uint32_t lv = 0;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t i = i0 + u * 32 + lane, pos = region + i;
-        row[u] = 0;
-        src0[u] = pos;
-        mult[u] = 1;
-        if (i < n_list) {
-          lv |= 1u << u;
-          row[u] = out.row[pos];
-          if (p > 1) src0[u] = out.src[pos];
-          if (out.mult) mult[u] = out.mult[pos];
+        for (int u = 0; u < kFuseU; ++u) {
+          const uint32_t i = i0 + u * 32 + lane;
+          row[u] = 0;
+          if (i < n_list) {
+            lv |= 1u << u;
+            row[u] = out.row[region + i];
+          }
         }
-      }
-      c_probe += __popc(lv);
-      lv = scan_probe_rows<U>(Pp, mp, fp, lv, row, e, out.mult ? mult : nullptr, &res->status);
-      c_hit += __popc(lv);
-      __syncwarp();  // every lane has read its entries before any is rewritten
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool hit = lv >> u & 1u;
-        const uint32_t hm = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-          const uint32_t pos = region + n_out + __popc(hm & lanemask_lt());
-          if (!Pp.last) out.h[p][src0[u]] = e[u];
-          out.row[pos] = row[u];
-          out.src[pos] = src0[u];
-          if (out.mult) out.mult[pos] = mult[u];
+        for (int u = 0; u < kFuseU; ++u) key[u] = (lv >> u & 1u) ? uint32_t(__ldg(kc + row[u])) : 0u;
+#pragma unroll
+        for (int u = 0; u < kFuseU; ++u)
+          if (lv >> u & 1u) sl[u] = __ldg(&Pp.ht[hash_root1(int32_t(key[u])) & mp]);
+        c_probe += __popc(lv);
+#pragma unroll
+        for (int u = 0; u < kFuseU; ++u) {
+          if (!(lv >> u & 1u)) continue;
+          uint32_t e = 0, cnt = 0;
+          if (root1_resolve(Pp.ht, mp, key[u], hash_root1(int32_t(key[u])) & mp, sl[u], e,
+                            cnt)) {
+            sl[u].z = e;
+            sl[u].w = cnt;
+          } else {
+            lv &= ~(1u << u);
+          }
         }
-        n_out += __popc(hm);
+        c_hit += __popc(lv);
+        // Each hit's position after the first probe (into key[]) and
+        // multiplicity (into the spent key words of its slot), read by every
+        // lane before any lane compacts.
+#pragma unroll
+        for (int u = 0; u < kFuseU; ++u) {
+          if (!(lv >> u & 1u)) continue;
+          const uint32_t i = region + i0 + u * 32 + lane;
+          key[u] = p > 1 ? out.src[i] : i;
+          if (out.mult) {
+            uint64_t m = out.mult[i];
+            if (Pp.last) m = mul_sat(m, sl[u].w, &res->status);
+            sl[u].x = uint32_t(m);
+            sl[u].y = uint32_t(m >> 32);
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kFuseU; ++u) {
+          const bool hit = lv >> u & 1u;
+          const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+          if (hit) {
+            const uint32_t pos = region + n_out + __popc(hm & lanemask_lt());
+            if (!Pp.last) out.h[p][key[u]] = sl[u].z;
+            if (out.mult) out.mult[pos] = (uint64_t(sl[u].y) << 32) | sl[u].x;
+            out.row[pos] = row[u];
+            out.src[pos] = key[u];
+          }
+          n_out += __popc(hm);
+        }
+        __syncwarp();
       }
     }
     n_list = n_out;
@@ -879,9 +954,49 @@ __global__ void __launch_bounds__(kThreads, 3) k_scan_fused(const __grid_constan
     scan_epilogue<R, true>(nd, sc, out, atoms, res, idx, row, mult, lv, &s_cnt, &s_base, s_min,
                            my_count, any);
   }
-  scan_block_totals(nd, res, s_min, s_red, my_count, any, surv, c_probe, c_hit);
-  if (blockIdx.x == 0 && tid == 0 && n_rows)
-    atomicAdd(&res->ctr[FJ_CTR_COVER_ITERS], (unsigned long long)n_rows);
+
+  // Warp totals into shared memory; the last warp of the block to arrive
+  // publishes the block's totals (no block barrier).
+  for (int o = 16; o; o >>= 1) {
+    my_count += __shfl_xor_sync(0xffffffffu, my_count, o);
+    surv += __shfl_xor_sync(0xffffffffu, surv, o);
+    c_probe += __shfl_xor_sync(0xffffffffu, c_probe, o);
+    c_hit += __shfl_xor_sync(0xffffffffu, c_hit, o);
+  }
+  const bool any_w = __any_sync(0xffffffffu, any);
+  __threadfence_block();  // every lane's shared-memory MINs before the arrival
+  __syncwarp();
+  uint32_t last = 0;
+  if (lane == 0) {
+    if (my_count) {
+      const unsigned long long old = atomicAdd(&s_tot[0], my_count);
+      if (old + my_count < old) atomicOr(&res->status, kStCountOverflow);
+    }
+    if (surv) atomicAdd(&s_tot[1], surv);
+    if (c_probe) atomicAdd(&s_tot[2], c_probe);
+    if (c_hit) atomicAdd(&s_tot[3], c_hit);
+    if (any_w) atomicOr(&s_tot[4], 1ull);
+    __threadfence_block();
+    last = atomicAdd(&s_done, 1u) == W - 1;
+  }
+  if (!__shfl_sync(0xffffffffu, last, 0)) return;
+  __threadfence_block();
+  const volatile unsigned long long* vt = s_tot;
+  if (nd.mode == kModeAggregate) {
+    if (lane == 0 && vt[0]) {
+      const unsigned long long old = atomicAdd(&res->count, vt[0]);
+      if (old + vt[0] < old) atomicOr(&res->status, kStCountOverflow);
+    }
+    if (vt[4])
+      atomicMin(&res->mins[lane], reinterpret_cast<volatile int32_t*>(s_min)[lane]);
+  }
+  if (lane == 0) {
+    if (vt[1]) atomicAdd(&res->ctr[FJ_CTR_SURVIVORS], vt[1]);
+    if (vt[2]) atomicAdd(&res->ctr[FJ_CTR_PROBES], vt[2]);
+    if (vt[3]) atomicAdd(&res->ctr[FJ_CTR_PROBE_HITS], vt[3]);
+    if (blockIdx.x == 0 && n_rows)
+      atomicAdd(&res->ctr[FJ_CTR_COVER_ITERS], (unsigned long long)n_rows);
+  }
 }
 
 // The survivor count to zero before a chunk.

@@ -32,18 +32,24 @@ FLAG_EAGER_ALL = 1
 FLAG_EAGER_ROOT = 2
 FLAG_TIMING = 4
 FLAG_TEST_TIMEOUT = 8
+FLAG_NO_FUSED_SCAN = 16
 CTR = {"cover_iters": 0, "probes": 1, "probe_hits": 2, "roots_built": 3, "subtries_forced": 4,
        "rows_regrouped": 5, "survivors": 6, "chunks": 7, "kernels": 8, "atom_built_mask": 9,
-       "expand_ns": 10, "expand_launches": 11, "build_ns": 12, "span_ns": 13}
+       "expand_ns": 10, "expand_launches": 11, "build_ns": 12, "span_ns": 13, "cover_policy": 14}
+CHOOSER_IN_DIM = 137
 
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "INVALID_PLAN", -3: "OOM", -4: "OUTPUT_OVERFLOW",
           -5: "COUNT_OVERFLOW", -6: "TIMEOUT", -7: "CUDA", -8: "UNSUPPORTED"}
 
 
 class FJError(RuntimeError):
-    def __init__(self, status, msg):
+    """A failed library call.  ``result`` is set for FJ_ERR_OUTPUT_OVERFLOW of
+    a materialized execution: the exact COUNT and the first list_limit rows."""
+
+    def __init__(self, status, msg, result=None):
         super().__init__(f"{ERRORS.get(status, status)}: {msg}")
         self.status = status
+        self.result = result
 
 
 class _Pred(ctypes.Structure):
@@ -82,6 +88,10 @@ class _Opts(ctypes.Structure):
                 ("model", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
 
 
+class _BushyNode(ctypes.Structure):
+    _fields_ = [("atom", ctypes.c_int), ("left", ctypes.c_int), ("right", ctypes.c_int)]
+
+
 class _Result(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("mins", ctypes.c_int32 * MAX_VARS),
                 ("min_valid", ctypes.c_uint8 * MAX_VARS), ("n_head", ctypes.c_int),
@@ -106,6 +116,8 @@ _sig = {
     "fj_binary_to_free_plan": ([_P(_Query), _P(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                 _P(_P(_Plan))], ctypes.c_int),
     "fj_plan_free": ([_P(_Plan)], None),
+    "fj_generic_join_plan": ([_P(_Query), _P(ctypes.c_int), ctypes.c_int, _P(_P(_Plan))],
+                             ctypes.c_int),
     "fj_ght_schema": ([_P(_Query), _P(_Plan), ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int),
                        _P(ctypes.c_int)], ctypes.c_int),
     "fj_node_covers": ([_P(_Query), _P(_Plan), ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)],
@@ -120,6 +132,8 @@ _sig = {
     "fj_prepared_free": ([_vp], None),
     "fj_batch_create": ([_vp, ctypes.c_int, _P(_vp), ctypes.c_int, _P(_vp)], ctypes.c_int),
     "fj_batch_execute": ([_vp, _P(_Result)], ctypes.c_int),
+    "fj_batch_launch": ([_vp], ctypes.c_int),
+    "fj_batch_results": ([_vp, _P(_Result)], ctypes.c_int),
     "fj_batch_free": ([_vp], None),
     "fj_model_create": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(_vp)],
                         ctypes.c_int),
@@ -131,11 +145,21 @@ _sig = {
     "fj_model_train_step": ([_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _P(ctypes.c_float)],
                             ctypes.c_int),
     "fj_model_last_error": ([], ctypes.c_char_p),
+    "fj_model_set_scaler": ([_vp, _vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "fj_model_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "fj_model_load": ([_vp, ctypes.c_char_p, ctypes.c_int, _P(_vp)], ctypes.c_int),
+    "fj_plan_features": ([_vp, _P(_Query), ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int), _vp],
+                         ctypes.c_int),
+    "fj_choose_plan": ([_vp, _P(_Query), _vp, ctypes.c_int, ctypes.c_uint64, _P(_P(_Plan)),
+                        _P(ctypes.c_int), _P(ctypes.c_int)], ctypes.c_int),
+    "fj_chooser_last_error": ([], ctypes.c_char_p),
     "fj_model_free": ([_vp], None),
     "fj_degree_histogram": ([_vp, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vp],
                             ctypes.c_int),
     "fj_stats_last_error": ([], ctypes.c_char_p),
     "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
+    "fj_execute_bushy": ([_vp, _P(_Query), _P(_BushyNode), ctypes.c_int, _P(_Opts), _P(_Result)],
+                         ctypes.c_int),
     "fj_result_free": ([_vp, _P(_Result)], None),
     "fj_join2_count_noalloc": ([_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp, _vp],
                                ctypes.c_int),
@@ -232,6 +256,17 @@ def binary_to_free_plan(atoms, order=None, factor=True):
     out = _P(_Plan)()
     _check(_lib.fj_binary_to_free_plan(q.ptr, _ints(order), len(order), int(bool(factor)),
                                        ctypes.byref(out)))
+    try:
+        return _plan_from_c(out)
+    finally:
+        _lib.fj_plan_free(out)
+
+
+def generic_join_plan(atoms, var_order):
+    """The Generic Join plan of a total variable order (Section 3.2, Eq. 3)."""
+    q = _QueryC(atoms)
+    out = _P(_Plan)()
+    _check(_lib.fj_generic_join_plan(q.ptr, _ints(var_order), len(var_order), ctypes.byref(out)))
     try:
         return _plan_from_c(out)
     finally:
@@ -364,10 +399,12 @@ class Result:
         self.counters = {k: int(res.counters[v]) for k, v in CTR.items()}
 
 
-def _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags):
+def _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags, model=None,
+          spin_limit=0):
     mv = _ints(min_vars or [])
     o = _Opts(int(batch_size), float(load_factor), COVER[cover], OUT[out_mode], int(list_limit),
-              len(min_vars or []), ctypes.cast(mv, _P(ctypes.c_int)), 0, None, int(flags))
+              len(min_vars or []), ctypes.cast(mv, _P(ctypes.c_int)), int(spin_limit),
+              model.handle if model is not None else None, int(flags))
     return o, mv
 
 
@@ -381,21 +418,71 @@ def _take_tuples(ctx, res, n_head):
 
 
 def execute(ctx, atoms, plan, head=None, out_mode="count", min_vars=None, batch_size=0,
-            load_factor=0.0, cover="static", list_limit=0, flags=0):
+            load_factor=0.0, cover="static", list_limit=0, flags=0, model=None, spin_limit=0):
     """One-shot fj_execute_plan.  Returns a :class:`Result`; materialized
     tuples come back as an (n, len(head)) int32 CUDA tensor in head order
-    (unsorted)."""
+    (unsorted).  ``cover="learned"`` needs ``model`` (a :class:`Model`)."""
     q, p = _QueryC(atoms, head), _PlanC(plan)
-    o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags)
+    o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags, model,
+                  spin_limit)
     res = _Result()
-    _check(_lib.fj_execute_plan(ctx.handle, q.ptr, p.ptr, ctypes.byref(o), ctypes.byref(res)))
+    st = _lib.fj_execute_plan(ctx.handle, q.ptr, p.ptr, ctypes.byref(o), ctypes.byref(res))
+    if st not in (0, -4):
+        _check(st)
+    msg = _lib.fj_last_error().decode()
     tuples = None
     try:
-        if out_mode == "materialize":
+        if out_mode == "materialize" and res.d_tuples:
             tuples = _take_tuples(ctx, res, res.n_head)
     finally:
         _lib.fj_result_free(ctx.handle, ctypes.byref(res))
-    return Result(res, tuples, min_vars or [])
+    out = Result(res, tuples, min_vars or [])
+    if st != 0:
+        raise FJError(st, msg, out)
+    return out
+
+
+def bushy_nodes(tree):
+    """Flatten a nested join tree -- an atom index, or a pair (left, right)
+    of trees -- into fj_bushy_node rows, the root last."""
+    nodes = []
+
+    def walk(t):
+        if isinstance(t, int):
+            nodes.append((t, -1, -1))
+        else:
+            left, right = walk(t[0]), walk(t[1])
+            nodes.append((-1, left, right))
+        return len(nodes) - 1
+
+    walk(tree)
+    return nodes
+
+
+def execute_bushy(ctx, atoms, tree, head=None, out_mode="count", min_vars=None, batch_size=0,
+                  load_factor=0.0, cover="static", list_limit=0, flags=0, model=None):
+    """fj_execute_bushy: run a bushy join tree (nested pairs of atom indices)
+    with its non-atom right children materialized first."""
+    q = _QueryC(atoms, head)
+    nodes = bushy_nodes(tree)
+    arr = (_BushyNode * len(nodes))(*[_BushyNode(*n) for n in nodes])
+    o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags, model)
+    res = _Result()
+    st = _lib.fj_execute_bushy(ctx.handle, q.ptr, arr, len(nodes), ctypes.byref(o),
+                               ctypes.byref(res))
+    if st not in (0, -4):
+        _check(st)
+    msg = _lib.fj_last_error().decode()
+    tuples = None
+    try:
+        if out_mode == "materialize" and res.d_tuples:
+            tuples = _take_tuples(ctx, res, res.n_head)
+    finally:
+        _lib.fj_result_free(ctx.handle, ctypes.byref(res))
+    out = Result(res, tuples, min_vars or [])
+    if st != 0:
+        raise FJError(st, msg, out)
+    return out
 
 
 def join2_count_noalloc(r_key, s_key, out, stream=None):
@@ -429,14 +516,16 @@ class Prepared:
     """fj_prepare / fj_build_colt_level / fj_execute_prepared / fj_reset_prepared."""
 
     def __init__(self, ctx, atoms, plan, head=None, out_mode="count", min_vars=None,
-                 batch_size=0, load_factor=0.0, cover="static", list_limit=0, flags=0):
+                 batch_size=0, load_factor=0.0, cover="static", list_limit=0, flags=0,
+                 model=None, spin_limit=0):
         self.ctx = ctx
         self.min_vars = list(min_vars or [])
         self.out_mode = out_mode
         # The library borrows the relations' columns: keep them alive.
         self._rels = [a["rel"] for a in atoms]
         q, p = _QueryC(atoms, head), _PlanC(plan)
-        o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags)
+        o, mv = _opts(out_mode, min_vars, batch_size, load_factor, cover, list_limit, flags,
+                      model, spin_limit)
         self.handle = _vp()
         _check(_lib.fj_prepare(ctx.handle, q.ptr, p.ptr, ctypes.byref(o), ctypes.byref(self.handle)))
         ctx._adopt(self)
@@ -492,6 +581,15 @@ class Batch:
     def execute(self):
         res = (_Result * max(1, len(self.preps)))()
         _check(_lib.fj_batch_execute(self.handle, res))
+        return [Result(res[i], None, p.min_vars) for i, p in enumerate(self.preps)]
+
+    def launch(self):
+        """Enqueue the batch (fj_batch_launch); :meth:`results` waits."""
+        _check(_lib.fj_batch_launch(self.handle))
+
+    def results(self):
+        res = (_Result * max(1, len(self.preps)))()
+        _check(_lib.fj_batch_results(self.handle, res))
         return [Result(res[i], None, p.min_vars) for i, p in enumerate(self.preps)]
 
     def free(self):
@@ -590,6 +688,27 @@ class Model:
                                              x.shape[0], float(lr), ctypes.byref(loss)))
         return float(loss.value)
 
+    def set_scaler(self, mean, scale):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        self._check(_lib.fj_model_set_scaler(self.handle, _vp(m.ctypes.data), _vp(sc.ctypes.data),
+                                             m.size))
+
+    def save(self, path):
+        self._check(_lib.fj_model_save(self.handle, str(path).encode()))
+
+    @classmethod
+    def load(cls, ctx, path, max_batch=8192):
+        m = cls.__new__(cls)
+        m.ctx = ctx
+        m.handle = _vp()
+        st = _lib.fj_model_load(ctx.handle, str(path).encode(), int(max_batch),
+                                ctypes.byref(m.handle))
+        if st != 0:
+            raise FJError(st, _lib.fj_model_last_error().decode())
+        m.n_params = int(_lib.fj_model_n_params(m.handle))
+        return m
+
     def free(self):
         if self.handle and self.ctx.handle:
             _lib.fj_model_free(self.handle)
@@ -618,3 +737,37 @@ def degree_histogram(ctx, col, mod=100, seed=0):
         raise FJError(st, _lib.fj_stats_last_error().decode())
     return out
 
+
+def plan_features(ctx, atoms, candidates):
+    """fj_plan_features: the chooser's features of each (order, cover policy
+    name) candidate, as a numpy float32 array (len(candidates), CHOOSER_IN_DIM)."""
+    q = _QueryC(atoms)
+    cands = list(candidates)
+    out = np.zeros((len(cands), CHOOSER_IN_DIM), dtype=np.float32)
+    orders = _ints([a for o, _ in cands for a in o])
+    pols = _ints([COVER[p] for _, p in cands])
+    st = _lib.fj_plan_features(ctx.handle, q.ptr, len(cands), orders, pols, _vp(out.ctypes.data))
+    if st != 0:
+        raise FJError(st, _lib.fj_chooser_last_error().decode())
+    return out
+
+
+def choose_plan(ctx, atoms, model=None, max_candidates=24, seed=0):
+    """fj_choose_plan: (plan, cover policy name, order) -- the candidate with
+    the smallest predicted work, or the declared order with the static cover
+    when ``model`` is None."""
+    q = _QueryC(atoms)
+    out = _P(_Plan)()
+    pol = ctypes.c_int(0)
+    order = (ctypes.c_int * len(atoms))()
+    st = _lib.fj_choose_plan(ctx.handle, q.ptr, model.handle if model is not None else None,
+                             int(max_candidates), int(seed), ctypes.byref(out), ctypes.byref(pol),
+                             order)
+    if st != 0:
+        raise FJError(st, _lib.fj_chooser_last_error().decode())
+    try:
+        plan = _plan_from_c(out)
+    finally:
+        _lib.fj_plan_free(out)
+    name = {v: k for k, v in COVER.items()}[pol.value]
+    return plan, name, [order[i] for i in range(len(atoms))]

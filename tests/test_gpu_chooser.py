@@ -2,9 +2,13 @@
 
 * The network's CUDA forward, backward and descent kernels against the
   float64 restatement in oracle/mlp.py (itself pinned by finite differences).
+* The chooser's features, plan choice, model file and learned cover policy
+  through the C ABI (fj_plan_features, fj_choose_plan, fj_model_save/load,
+  FJ_COVER_LEARNED).
 * The chooser trained on work the exact engine reports for engine-generated
-  queries: on held-out queries its orders give exactly the results of the
-  declared order (the converted binary plan, its fallback) and less work.
+  queries: on held-out queries its choices give exactly the results of the
+  declared order (the converted binary plan, its fallback) with less work
+  than it and no more than the fewest-keys cover.
 """
 
 import numpy as np
@@ -80,49 +84,124 @@ def test_model_kernels_match_oracle(fj, ctx):
     m.free()
 
 
-def _engine_samples(fj, ctx, queries):
-    """(features, log2 work, count) of every candidate order of each query."""
-    out = []
-    for atoms, _ in queries:
+def _features_by_definition(fj, ctx, atoms, order, policy):
+    """The documented feature layout (include/fj.h, FJ_CHOOSER_IN_DIM),
+    written out here from fj.degree_histogram and the row counts."""
+    import torch
+    sets = [set(a["vars"]) for a in atoms]
+    n_vars = len(set().union(*sets))
+    cyclic = sum(len(v) for v in sets) - n_vars >= len(atoms)
+    f, bound = [], set()
+    for pos in range(4):
+        if pos >= len(order):
+            f.extend([0.0] * 33)
+            continue
+        a = order[pos]
+        with_ = (sets[order[1]] if len(order) > 1 else set()) if pos == 0 else bound
+        j = next((k for k, v in enumerate(atoms[a]["vars"]) if v in with_), 0)
+        col = torch.from_numpy(np.ascontiguousarray(atoms[a]["cols"][j])).cuda()
+        f.append(np.log2(len(atoms[a]["cols"][0]) + 1.0) / 32.0)
+        f.extend(fj.degree_histogram(ctx, col, mod=100, seed=31 * a + j))
+        bound |= sets[a]
+    f.extend([len(order) / 8.0, n_vars / 32.0, float(cyclic), 1.0,
+              1.0 if policy == "fewest" else 0.0])
+    return np.asarray(f, dtype=np.float32)
+
+
+def test_plan_features_follow_their_definition(fj, ctx):
+    rng = np.random.default_rng(3)
+    for q in range(4):
+        atoms, _ = G.chooser_query(q, 2_000, 9_000)
         dev, _ = device_atoms(fj, ctx, atoms)
-        hists = C.atom_histograms(ctx, atoms)
-        orders = C.candidate_orders([a["vars"] for a in atoms])
-        rows = []
-        for o in orders:
-            r = fj.execute(ctx, dev, fj.binary_to_free_plan(dev, o, factor=True),
-                           out_mode="count")
-            rows.append((C.order_features(atoms, o, hists), np.log2(C.work(r) + 1.0), r.count))
-        out.append((atoms, dev, hists, orders, rows))
-    return out
+        cands = C.training_candidates([a["vars"] for a in atoms], 3, rng)
+        got = fj.plan_features(ctx, dev, cands)
+        assert got.shape == (len(cands), fj.CHOOSER_IN_DIM)
+        for row, (order, pol) in zip(got, cands):
+            want = _features_by_definition(fj, ctx, atoms, order, pol)
+            np.testing.assert_allclose(row, want, rtol=1e-6, atol=1e-7)
+    with pytest.raises(fj.FJError):
+        fj.plan_features(ctx, dev, [([0, 0, 1, 2, 3], "static")])
+
+
+def test_choose_plan_without_model_is_the_converted_binary_plan(fj, ctx):
+    atoms, _ = G.chooser_query(1, 2_000, 5_000)
+    dev, _ = device_atoms(fj, ctx, atoms)
+    plan, pol, order = fj.choose_plan(ctx, dev, None)
+    assert order == list(range(len(atoms))) and pol == "static"
+    assert plan == fj.binary_to_free_plan(dev, order, factor=True)
+
+
+def test_model_save_load_and_learned_cover(fj, ctx, tmp_path):
+    """A saved model loads with the same parameters, scaler and predictions;
+    FJ_COVER_LEARNED runs the policy the model predicts cheaper for the
+    plan, and its results equal the oracle's."""
+    import torch
+
+    import oracle
+    rng = np.random.default_rng(5)
+    d = fj.CHOOSER_IN_DIM
+    m = fj.Model(ctx, d, 32, 16, max_batch=64)
+    m.set_params(C.init_params(d, 32, 16, seed=7))
+    mean = rng.normal(0, 0.1, d).astype(np.float32)
+    scale = rng.uniform(0.5, 2.0, d).astype(np.float32)
+    m.set_scaler(mean, scale)
+    path = tmp_path / "chooser.fjm"
+    m.save(path)
+    m2 = fj.Model.load(ctx, path, max_batch=64)
+    np.testing.assert_array_equal(m2.params(), m.params())
+    x = rng.normal(0, 1, (40, d)).astype(np.float32)
+    xs = torch.from_numpy((x - mean) / scale).cuda()
+    np.testing.assert_array_equal(m2.forward(xs).cpu().numpy(), m.forward(xs).cpu().numpy())
+    (tmp_path / "bad.fjm").write_bytes(b"not a model")
+    with pytest.raises(fj.FJError):
+        fj.Model.load(ctx, tmp_path / "bad.fjm")
+    for q in range(6):
+        atoms, _ = G.chooser_query(q, 2_000, 6_000)
+        dev, _ = device_atoms(fj, ctx, atoms)
+        plan = fj.binary_to_free_plan(dev, list(range(len(atoms))), factor=True)
+        want = oracle.binary_join(atoms)[0]
+        got = fj.execute(ctx, dev, plan, out_mode="count", cover="learned", model=m2)
+        assert got.count == want
+        f = fj.plan_features(ctx, dev, [(list(range(len(atoms))), p) for p in C.POLICIES])
+        pred = m2.forward(torch.from_numpy((f - mean) / scale).cuda()).cpu().numpy()
+        assert got.counters["cover_policy"] == (1 if pred[1] < pred[0] else 0)
+    with pytest.raises(fj.FJError):
+        fj.execute(ctx, dev, plan, out_mode="count", cover="learned")  # no model
+    m.free()
+    m2.free()
 
 
 def test_chooser_gain(fj, ctx):
-    import torch
-    train_q = [G.chooser_query(q, 3_000, 20_000) for q in range(120)]
-    test_q = [G.chooser_query(q, 20_000, 80_000) for q in range(1000, 1016)]
-    train = _engine_samples(fj, ctx, train_q)
-    for *_, rows in train:  # every order of a query gives the same count
-        assert len({c for _, _, c in rows}) == 1
-    x = np.stack([f for *_, rows in train for f, _, _ in rows])
-    y = np.array([w for *_, rows in train for _, w, _ in rows], dtype=np.float32)
-    scaler = C.fit_scaler(x)
-    mu, sd = float(y.mean()), float(y.std() + 1e-6)
-    model = fj.Model(ctx, C.IN_DIM, 128, 64, max_batch=8192)
-    model.set_params(C.init_params(C.IN_DIM, 128, 64, seed=1))
-    losses = C.train(model, torch.from_numpy(C.standardize(x, scaler)).cuda(),
-                     torch.from_numpy((y - mu) / sd).cuda())
+    """Trained on the engine's work for generated queries, the chooser
+    (fj_choose_plan: order and cover policy together) does less work on
+    held-out queries than the plain converted binary plan and no more than
+    the fewest-keys cover alone, with identical results."""
+    rng = np.random.default_rng(0)
+    xs, ys = [], []
+    for q in range(160):
+        atoms, _ = G.chooser_query(q, 3_000, 20_000)
+        dev, _ = device_atoms(fj, ctx, atoms)
+        rows = C.samples(fj, ctx, dev, C.training_candidates([a["vars"] for a in atoms], 6, rng))
+        assert len({c for _, _, c in rows}) == 1  # every candidate gives the same count
+        xs += [f for f, _, _ in rows]
+        ys += [w for _, w, _ in rows]
+    model, losses = C.fit(fj, ctx, np.stack(xs), np.array(ys))
     assert losses[-1] < 0.6 * losses[0]
-    tot_declared = tot_chosen = tot_best = 0.0
-    for atoms, dev, hists, orders, rows in _engine_samples(fj, ctx, test_q):
-        chosen = C.choose(model, atoms, orders, hists, scaler)
-        i = orders.index(chosen)
-        assert rows[i][2] == rows[0][2]          # bit-exact whatever it picks
-        tot_declared += rows[0][1]
-        tot_chosen += rows[i][1]
-        tot_best += min(w for _, w, _ in rows)
-    print(f"log2 work summed over held-out queries: declared {tot_declared:.1f}, "
-          f"chosen {tot_chosen:.1f}, best {tot_best:.1f}")
-    assert tot_chosen < tot_declared
+    tot = {"plain": 0.0, "fewest": 0.0, "learned": 0.0}
+    for q in range(1000, 1024):
+        atoms, _ = G.chooser_query(q, 20_000, 80_000)
+        dev, _ = device_atoms(fj, ctx, atoms)
+        declared = fj.binary_to_free_plan(dev, list(range(len(atoms))), factor=True)
+        plan, pol, _ = fj.choose_plan(ctx, dev, model)
+        runs = {"plain": fj.execute(ctx, dev, declared, out_mode="count"),
+                "fewest": fj.execute(ctx, dev, declared, out_mode="count", cover="fewest"),
+                "learned": fj.execute(ctx, dev, plan, out_mode="count", cover=pol)}
+        assert len({r.count for r in runs.values()}) == 1  # bit-exact whatever it picks
+        for k, r in runs.items():
+            tot[k] += np.log2(C.work(r) + 1.0)
+    print("log2 work summed over held-out queries:", {k: round(v, 1) for k, v in tot.items()})
+    assert tot["learned"] < tot["plain"]
+    assert tot["learned"] <= tot["fewest"]
     model.free()
 
 

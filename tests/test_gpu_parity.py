@@ -246,3 +246,107 @@ def test_context_close_releases_live_children(fj):
     del p, atoms
     gc.collect()
     assert want == oracle.binary_join(G.triangle_query(e))[0]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_ablation_configurations_agree(fj, ctx, seed):
+    """The ablation configurations (simple trie, simple lazy trie, batch
+    sizes, no one-launch scan) and the Generic Join baseline give the
+    oracle's bag on random queries."""
+    atoms = G.random_query(700 + seed, max_atoms=4, max_rows=80, domain=6, max_vars=5,
+                           max_arity=3)
+    atom_vars = [a["vars"] for a in atoms]
+    head = oracle.query_vars(atoms)
+    want_c, want_m, want_t = oracle.binary_join(atoms, head=head, min_vars=head[:2],
+                                                materialize=True)
+    dev, _ = device_atoms(fj, ctx, atoms)
+    fplan = fj.binary_to_free_plan(dev, list(range(len(atoms))), factor=True)
+    gplan = fj.generic_join_plan(dev, head)
+    cfgs = [(fplan, fj.FLAG_EAGER_ALL, 2048, "static"), (fplan, fj.FLAG_EAGER_ROOT, 2048, "static"),
+            (fplan, fj.FLAG_NO_FUSED_SCAN, 256, "static"), (fplan, fj.FLAG_NO_FUSED_SCAN, 4096, "fewest"),
+            (gplan, fj.FLAG_EAGER_ALL | fj.FLAG_NO_FUSED_SCAN, 256, "fewest")]
+    for plan, flags, bs, cover in cfgs:
+        got = fj.execute(ctx, dev, plan, head=head, out_mode="materialize", flags=flags,
+                         batch_size=bs, cover=cover)
+        assert got.count == want_c, (flags, bs, cover)
+        np.testing.assert_array_equal(sort_rows(got.tuples.cpu().numpy()), want_t)
+        got = fj.execute(ctx, dev, plan, head=head, out_mode="count_min", min_vars=head[:2],
+                         flags=flags, batch_size=bs, cover=cover)
+        assert (got.count, got.mins) == (want_c, want_m), (flags, bs, cover)
+
+
+def test_ablation_star_join_eager_and_generic_join(fj, ctx):
+    """The star join under every trie variant and as a Generic Join: the
+    four-key fact level stays a vector under the eager flags."""
+    fact, dims = G.star_schema(n_fact=200_000, dims=(2000, 5000, 10000, 20000), s=1.1, seed=6)
+    theta = 300_000_000
+    atoms = G.star_query(fact, dims, theta=theta)
+    want = closed.star_join_direct(fact["cols"], [tuple(d["cols"]) for d in dims], [theta] * 4)
+    dev, _ = device_atoms(fj, ctx, atoms)
+    fplan = fj.binary_to_free_plan(dev, [0, 1, 2, 3, 4], factor=True)
+    gplan = fj.generic_join_plan(dev, list(range(8)))
+    for plan, flags, cover in [(fplan, fj.FLAG_EAGER_ALL, "static"),
+                               (fplan, fj.FLAG_EAGER_ROOT, "static"),
+                               (fplan, fj.FLAG_NO_FUSED_SCAN, "static"),
+                               (gplan, fj.FLAG_EAGER_ALL | fj.FLAG_NO_FUSED_SCAN, "fewest")]:
+        got = fj.execute(ctx, dev, plan, out_mode="count_min", min_vars=[4, 5, 6, 7],
+                         flags=flags, batch_size=256, cover=cover)
+        assert (got.count, got.mins) == want, (plan is gplan, flags)
+
+
+def test_list_limit_overflow_keeps_exact_count_and_rows(fj, ctx):
+    """FJ_ERR_OUTPUT_OVERFLOW: the COUNT stays exact and the first
+    list_limit rows come back, each a row of the oracle's bag."""
+    e = G.uniform_digraph(400, 6000, seed=21)
+    atoms = G.triangle_query(e)
+    want = oracle.generic_join(atoms, materialize=True)
+    dev, _ = device_atoms(fj, ctx, atoms)
+    plan = [[(0, (0, 1)), (1, (1,)), (2, (0,))], [(1, (2,)), (2, (2,))]]
+    limit = want[0] // 3
+    with pytest.raises(fj.FJError) as ei:
+        fj.execute(ctx, dev, plan, out_mode="materialize", list_limit=limit)
+    err = ei.value
+    assert err.status == -4 and err.result is not None
+    assert err.result.count == want[0]
+    rows = err.result.tuples.cpu().numpy()
+    assert len(rows) == limit
+    bag = {tuple(r) for r in want[2].tolist()}
+    assert all(tuple(r) in bag for r in rows.tolist())
+    # Within the limit the listing is complete.
+    got = fj.execute(ctx, dev, plan, out_mode="materialize", list_limit=want[0])
+    np.testing.assert_array_equal(sort_rows(got.tuples.cpu().numpy()), want[2])
+
+
+def test_count_overflow_is_reported(fj, ctx):
+    """A product above 2^64 - 1 (five relations of 10,000 equal keys: 10^20
+    combinations) fails with FJ_ERR_COUNT_OVERFLOW instead of wrapping."""
+    rels = [{"name": f"R{i}", "cols": [np.zeros(10_000, dtype=np.int32)]} for i in range(5)]
+    atoms = [G.atom(r, [0]) for r in rels]
+    dev, _ = device_atoms(fj, ctx, atoms)
+    plan = fj.binary_to_free_plan(dev, list(range(5)), factor=True)
+    with pytest.raises(fj.FJError) as ei:
+        fj.execute(ctx, dev, plan, out_mode="count")
+    assert ei.value.status == -5
+    # Four of them fit: 10^16.
+    got = fj.execute(ctx, dev[:4], fj.binary_to_free_plan(dev[:4], list(range(4))), out_mode="count")
+    assert got.count == 10**16
+
+
+def test_materialized_output_above_the_first_buffer_is_retried(fj, ctx):
+    """The output buffer starts at 2^20 rows; a larger listing is sized
+    exactly and run again, and every row comes back."""
+    r = {"name": "R", "cols": [np.arange(1200, dtype=np.int32) % 3, np.arange(1200, dtype=np.int32)]}
+    s = {"name": "S", "cols": [np.arange(1500, dtype=np.int32) % 3, np.arange(1500, dtype=np.int32)]}
+    atoms = [G.atom(r, [0, 1]), G.atom(s, [0, 2])]
+    want_c = 3 * 400 * 500
+    assert want_c > 1 << 20 is False or want_c < 1 << 20  # sanity of the arithmetic below
+    big = {"name": "S", "cols": [np.zeros(1000, dtype=np.int32), np.arange(1000, dtype=np.int32)]}
+    rb = {"name": "R", "cols": [np.zeros(1100, dtype=np.int32), np.arange(1100, dtype=np.int32)]}
+    atoms = [G.atom(rb, [0, 1]), G.atom(big, [0, 2])]
+    dev, _ = device_atoms(fj, ctx, atoms)
+    plan = fj.binary_to_free_plan(dev, [0, 1])
+    got = fj.execute(ctx, dev, plan, out_mode="materialize")
+    assert got.count == 1100 * 1000 > 1 << 20
+    t = got.tuples.cpu().numpy()
+    assert len(t) == got.count
+    assert len({(a, b) for _, a, b in t.tolist()}) == 1100 * 1000

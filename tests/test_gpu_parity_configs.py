@@ -31,7 +31,7 @@ def test_star_join_full_size_as_benchmarked(fj, ctx):
     dev, _ = device_atoms(fj, ctx, atoms)
     plan = fj.binary_to_free_plan(dev, [0, 1, 2, 3, 4], factor=True)
     mins = [4, 5, 6, 7]
-    prep = fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins, batch_size=2048,
+    prep = fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins, batch_size=1024,
                        flags=fj.FLAG_TIMING)
     for _ in range(3):
         prep.reset()

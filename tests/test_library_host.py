@@ -100,3 +100,25 @@ def test_invalid_plans_are_rejected(fjm):
         ok, why = fjm.validate_plan(tri, plan)
         assert not ok, name
         assert why
+
+
+def test_generic_join_plan_is_one_node_per_variable(fjm):
+    """fj_generic_join_plan (Section 3.2, Eq. 3): node k holds R(x_k) of every
+    atom containing x_k, in atom order; every such plan is valid."""
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from fjtest import gj_plan
+    rng = np.random.default_rng(4)
+    for seed in range(60):
+        atoms = G.random_query(seed, max_atoms=5, max_vars=6, max_arity=3)
+        atom_vars = [a["vars"] for a in atoms]
+        nv = sorted({v for vs in atom_vars for v in vs})
+        order = [int(v) for v in rng.permutation(nv)]
+        plan = fjm.generic_join_plan(_atoms(atom_vars), order)
+        want = [[(a, (x,)) for a, vs in enumerate(atom_vars) if x in vs] for x in order]
+        assert plan == want == gj_plan(atom_vars, order)
+        assert fjm.validate_plan(_atoms(atom_vars), plan)[0]
+    with pytest.raises(fjm.FJError):
+        fjm.generic_join_plan(_atoms([[0, 1], [1, 2]]), [0, 1])      # a variable missing
+    with pytest.raises(fjm.FJError):
+        fjm.generic_join_plan(_atoms([[0, 1], [1, 2]]), [0, 1, 1])   # a variable twice
