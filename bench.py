@@ -737,38 +737,38 @@ def run_chooser(args, rank, world):
         return [{"rel": ctx.relation([torch.from_numpy(c).to(dev) for c in a["cols"]]),
                  "vars": a["vars"]} for a in atoms]
 
+    # Training: engine-generated queries, six orders x two cover policies
+    # each, labelled with the engine's work (untimed).
     t_train = time.perf_counter()
+    rng = np.random.default_rng(0)
     xs, ys = [], []
-    for q in range(120):
-        atoms, _ = G.chooser_query(q, 3_000, 20_000)
+    for q in range(args.train_queries):
+        atoms, _ = G.chooser_query(q, 2_000, 20_000)
         d = device(atoms)
-        hists = C.atom_histograms(ctx, atoms)
-        for o in C.candidate_orders([a["vars"] for a in atoms]):
-            r = fj.execute(ctx, d, fj.binary_to_free_plan(d, o, factor=True), out_mode="count")
-            xs.append(C.order_features(atoms, o, hists))
-            ys.append(np.log2(C.work(r) + 1.0))
-    x = np.stack(xs)
-    y = np.asarray(ys, dtype=np.float32)
-    scaler = C.fit_scaler(x)
-    model = fj.Model(ctx, C.IN_DIM, 128, 64, max_batch=8192)
-    model.set_params(C.init_params(C.IN_DIM, 128, 64, seed=1))
-    losses = C.train(model, torch.from_numpy(C.standardize(x, scaler)).to(dev),
-                     torch.from_numpy((y - y.mean()) / (y.std() + 1e-6)).to(dev))
+        for f, w, _ in C.samples(fj, ctx, d, C.training_candidates([a["vars"] for a in atoms],
+                                                                   6, rng)):
+            xs.append(f)
+            ys.append(w)
+        for a in d:
+            a["rel"].release()
+    model, losses = C.fit(fj, ctx, np.stack(xs), np.asarray(ys, dtype=np.float32))
     t_train = time.perf_counter() - t_train
 
+    # Held-out queries: the plain converted binary plan, the same plan with
+    # the fewest-keys cover, and the chooser's plan and policy.
     policies = {"plain": [], "fewest": [], "learned": []}
     in_tuples = 0
+    choices = []
     for q in range(2000, 2000 + args.n_queries):
-        atoms, _ = G.chooser_query(q, args.min_rows, args.max_rows)
+        atoms, kind = G.chooser_query(q, args.min_rows, args.max_rows)
         d = device(atoms)
         in_tuples += sum(len(a["cols"][0]) for a in atoms)
-        orders = C.candidate_orders([a["vars"] for a in atoms])
-        chosen = C.choose(model, atoms, orders, C.atom_histograms(ctx, atoms), scaler)
-        declared = fj.binary_to_free_plan(d, orders[0], factor=True)
+        declared = fj.binary_to_free_plan(d, list(range(len(atoms))), factor=True)
+        plan, pol, order = fj.choose_plan(ctx, d, model)
+        choices.append({"kind": kind, "order": order, "cover": pol})
         policies["plain"].append(fj.Prepared(ctx, d, declared, out_mode="count"))
         policies["fewest"].append(fj.Prepared(ctx, d, declared, out_mode="count", cover="fewest"))
-        policies["learned"].append(fj.Prepared(ctx, d, fj.binary_to_free_plan(d, chosen, factor=True),
-                                               out_mode="count"))
+        policies["learned"].append(fj.Prepared(ctx, d, plan, out_mode="count", cover=pol))
     flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
@@ -816,13 +816,17 @@ def run_chooser(args, rank, world):
                                    f"seeds 2005..): 5-relation snowflakes and 5-cycles, rows "
                                    f"log-uniform in [{args.min_rows}, {args.max_rows}], Zipf "
                                    f"keys s in [0.8, 1.6]; COUNT(*)",
-                       "training": "120 generated queries of 3K-20K rows, every connected "
-                                   "order, label log2 engine work; 60 epochs on the library's "
-                                   "kernels",
+                       "training": f"{args.train_queries} generated queries of 2K-20K rows, the "
+                                   "declared order and five other connected orders each, both "
+                                   "cover policies, label log2 engine work; 60 epochs on the "
+                                   "library's kernels",
                        "l2": L2_NOTE, "in_tuples": in_tuples},
             "result": {"out_tuples": out_tuples},
             "policies": {k: {"ms_per_step": v, "value": tot / (v / 1000)} for k, v in ms.items()},
-            "train": {"seconds": t_train, "samples": int(len(y)), "loss_first": losses[0],
+            "speedup_vs_plain": ms["plain"] / ms["learned"],
+            "speedup_vs_fewest": ms["fewest"] / ms["learned"],
+            "choices": choices,
+            "train": {"seconds": t_train, "samples": len(ys), "loss_first": losses[0],
                       "loss_last": losses[-1]},
             "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
             "gpu_launches": None, "impl": "fj"}
@@ -960,6 +964,7 @@ def main():
     ap.add_argument("--workload", default="star",
                     choices=["star", "rmat-triangle", "batched", "chooser", "ablation"])
     ap.add_argument("--rmat-scale", type=int, default=18)
+    ap.add_argument("--train-queries", type=int, default=10_000)
     ap.add_argument("--min-rows", type=int, default=50_000)
     ap.add_argument("--n-queries", type=int, default=256)
     ap.add_argument("--max-rows", type=int, default=2_000_000)

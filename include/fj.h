@@ -428,6 +428,29 @@ typedef struct {
 fj_status fj_execute_bushy(fj_ctx* ctx, const fj_query* query, const fj_bushy_node* nodes,
                            int n_nodes, const fj_exec_opts* opts, fj_result* out);
 
+/* Layout of an FJ_OUT_FACTORIZED result of a prepared plan: each of its
+ * n_out rows has *width int32 words -- the values of the *n_prefix head
+ * variables prefix_vars[0..*n_prefix) (in head order; capacity
+ * FJ_MAX_VARS), the row's multiplicity as two words (low first), and for
+ * each of the *n_tails trailing nodes (in plan order; tail_atoms[t] their
+ * atoms, capacity FJ_MAX_NODES) the first offset and the length of the
+ * COLT vector of that atom the row reaches.  The bag the row stands for is
+ * its prefix values, repeated multiplicity times, crossed with the base-table
+ * rows of every tail vector (their values of the tail's variables).
+ * Errors: FJ_ERR_INVALID_ARG. */
+fj_status fj_prepared_factor_layout(const fj_prepared* prep, int* width, int* n_prefix,
+                                    int* prefix_vars, int* n_tails, int* tail_atoms);
+
+/* Expand the factorized result `res` (the plan's last execution; its COLT
+ * vectors still in place) into res->count flat tuples in head order, written
+ * row-major to the device buffer d_dst of dst_rows x n_head int32.  Tuples
+ * come in factorized-row order; within a row the multiplicity copies vary
+ * slowest and the last tail fastest.  Synchronizes the stream.  Errors:
+ * FJ_ERR_INVALID_ARG (another result, or too small a buffer), FJ_ERR_OOM,
+ * FJ_ERR_CUDA. */
+fj_status fj_prepared_expand(fj_prepared* prep, const fj_result* res, int32_t* d_dst,
+                             uint64_t dst_rows);
+
 /* Copy a materialized result's rows (n_out x n_head int32) to `dst`, a
  * device pointer if dst_is_device != 0 else a host pointer.  Synchronizes the
  * stream.  FJ_ERR_INVALID_ARG if the result holds no tuples. */

@@ -1203,8 +1203,6 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
   if (opts) P->opts = *opts;
   if (P->opts.out_mode < FJ_OUT_MATERIALIZE || P->opts.out_mode > FJ_OUT_FACTORIZED)
     fail(FJ_ERR_INVALID_ARG, "bad out_mode");
-  if (P->opts.out_mode == FJ_OUT_FACTORIZED)
-    fail(FJ_ERR_UNSUPPORTED, "factorized output: the node kernels do not write it yet");
   if (P->opts.cover_policy < FJ_COVER_STATIC || P->opts.cover_policy > FJ_COVER_LEARNED)
     fail(FJ_ERR_INVALID_ARG, "bad cover_policy");
   if (P->opts.cover_policy == FJ_COVER_LEARNED) {
@@ -1382,6 +1380,96 @@ static void batch_free(fj_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   delete B;
+}
+
+// ---------------------------------------------------------------------------
+// Expansion of a factorized result into flat head-order tuples.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct FactorExpandDev {
+  int width, n_pre, n_tail, n_head;
+  // Per head position: the prefix column (src >= 0), or the tail (-1 - t)
+  // and its atom column.
+  int src[FJ_MAX_VARS];
+  int tcol[FJ_MAX_VARS];
+  const uint32_t* perm[FJ_MAX_NODES];
+  const int32_t* cols[FJ_MAX_NODES][FJ_MAX_ARITY];
+};
+
+// Bag size of every factorized row: multiplicity times the tail lengths.
+__global__ void k_factor_fan(const int32_t* __restrict__ rows, uint64_t n, FactorExpandDev fx,
+                             unsigned long long* fan) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    const int32_t* r = rows + i * fx.width;
+    unsigned long long m = uint64_t(uint32_t(r[fx.n_pre])) | uint64_t(uint32_t(r[fx.n_pre + 1])) << 32;
+    for (int t = 0; t < fx.n_tail; ++t) m *= uint32_t(r[fx.n_pre + 3 + 2 * t]);
+    fan[i] = m;
+  }
+}
+
+// One thread per factorized row writes its tuples at offset off[i]: the
+// multiplicity copies outermost, then the tails' vectors in mixed radix.
+__global__ void k_factor_expand(const int32_t* __restrict__ rows, uint64_t n, FactorExpandDev fx,
+                                const unsigned long long* __restrict__ off,
+                                const unsigned long long* __restrict__ fan, int32_t* out) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    const int32_t* r = rows + i * fx.width;
+    for (unsigned long long j = 0; j < fan[i]; ++j) {
+      int32_t* o = out + (off[i] + j) * fx.n_head;
+      uint32_t trow[FJ_MAX_NODES];
+      unsigned long long q = j;
+      for (int t = fx.n_tail - 1; t >= 0; --t) {
+        const uint32_t cn = uint32_t(r[fx.n_pre + 3 + 2 * t]);
+        trow[t] = fx.perm[t][uint32_t(r[fx.n_pre + 2 + 2 * t]) + uint32_t(q % cn)];
+        q /= cn;
+      }
+      for (int h = 0; h < fx.n_head; ++h) {
+        const int s = fx.src[h];
+        o[h] = s >= 0 ? r[s] : fx.cols[-1 - s][fx.tcol[h]][trow[-1 - s]];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+static void factor_layout(const fj_prepared* P, FactorExpandDev& fx) {
+  if (!P->factorized) fail(FJ_ERR_INVALID_ARG, "the plan was not prepared with FJ_OUT_FACTORIZED");
+  const NodeDev& N = P->nd[P->last];
+  fx.width = P->out_width;
+  fx.n_pre = N.n_pre;
+  fx.n_tail = N.n_tail;
+  fx.n_head = int(P->q.head.size());
+  for (int h = 0; h < fx.n_head; ++h) {
+    const int v = P->q.head[h];
+    fx.src[h] = 0;
+    fx.tcol[h] = 0;
+    bool found = false;
+    for (int k = 0; k < N.n_pre && !found; ++k)
+      if (N.pre_var[k] == v) {
+        fx.src[h] = k;
+        found = true;
+      }
+    for (int t = 0; t < N.n_tail && !found; ++t) {
+      const int node = P->tail_start + t;
+      const PSub& sa = P->plan[node][0];
+      if (std::find(sa.vars.begin(), sa.vars.end(), v) == sa.vars.end()) continue;
+      const auto& av = P->q.atom_vars[sa.atom];
+      fx.src[h] = -1 - t;
+      fx.tcol[h] = int(std::find(av.begin(), av.end(), v) - av.begin());
+      found = true;
+    }
+    if (!found) fail(FJ_ERR_INVALID_ARG, "internal: a head variable is in no factor");
+  }
+  for (int t = 0; t < N.n_tail; ++t) {
+    const AtomDev& a = P->host_atoms[N.tail[t].atom];
+    fx.perm[t] = a.perm;
+    for (int j = 0; j < FJ_MAX_ARITY; ++j) fx.cols[t][j] = a.cols[j];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1724,6 +1812,58 @@ fj_status fj_execute_plan(fj_ctx* ctx, const fj_query* query, const fj_plan* pla
   if (P) prepared_release(P);
   if (st != FJ_OK) set_error(get_error());
   return st;
+}
+
+fj_status fj_prepared_factor_layout(const fj_prepared* P, int* width, int* n_prefix,
+                                    int* prefix_vars, int* n_tails, int* tail_atoms) {
+  return guarded([&] {
+    if (!P || !width || !n_prefix || !prefix_vars || !n_tails || !tail_atoms)
+      fail(FJ_ERR_INVALID_ARG, "NULL argument");
+    FactorExpandDev fx{};
+    factor_layout(P, fx);
+    const NodeDev& N = P->nd[P->last];
+    *width = fx.width;
+    *n_prefix = N.n_pre;
+    for (int k = 0; k < N.n_pre; ++k) prefix_vars[k] = N.pre_var[k];
+    *n_tails = N.n_tail;
+    for (int t = 0; t < N.n_tail; ++t) tail_atoms[t] = N.tail[t].atom;
+  });
+}
+
+fj_status fj_prepared_expand(fj_prepared* P, const fj_result* res, int32_t* d_dst,
+                             uint64_t dst_rows) {
+  return guarded([&] {
+    if (!P || !res || (!d_dst && res->count)) fail(FJ_ERR_INVALID_ARG, "NULL argument");
+    FactorExpandDev fx{};
+    factor_layout(P, fx);
+    if (res->d_tuples != P->d_out) fail(FJ_ERR_INVALID_ARG, "not this plan's last result");
+    if (dst_rows < res->count) fail(FJ_ERR_INVALID_ARG, "the destination holds fewer rows than COUNT");
+    const uint64_t n = res->n_out;
+    if (n == 0) return;
+    fj_ctx* c = P->ctx;
+    cudaStream_t s = c->stream;
+    unsigned long long* fan = dalloc<unsigned long long>(c, n);
+    unsigned long long* off = dalloc<unsigned long long>(c, n);
+    std::vector<unsigned long long> h(n);
+    k_factor_fan<<<blocks_for(n, 256, c->n_sm * 8), 256, 0, s>>>(res->d_tuples, n, fx, fan);
+    CK_LAUNCH("factor fan");
+    CK(cudaMemcpyAsync(h.data(), fan, n * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    unsigned long long acc = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      const unsigned long long f = h[i];
+      h[i] = acc;
+      acc += f;
+    }
+    if (acc != res->count) fail(FJ_ERR_CUDA, "internal: factorized rows disagree with COUNT");
+    CK(cudaMemcpyAsync(off, h.data(), n * 8, cudaMemcpyHostToDevice, s));
+    k_factor_expand<<<blocks_for(n, 128, c->n_sm * 8), 128, 0, s>>>(res->d_tuples, n, fx, off, fan,
+                                                                    d_dst);
+    CK_LAUNCH("factor expand");
+    CK(cudaStreamSynchronize(s));
+    dfree(c, fan);
+    dfree(c, off);
+  });
 }
 
 fj_status fj_result_copy_tuples(fj_ctx* c, const fj_result* res, void* dst, int dst_is_device) {

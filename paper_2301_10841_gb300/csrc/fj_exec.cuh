@@ -190,6 +190,51 @@ __device__ __forceinline__ bool ht_resolve(const uint4* __restrict__ ht, uint32_
   return false;
 }
 
+// Factorized output (FJ_OUT_FACTORIZED, the result in trie form of
+// Section 4.4): a live element becomes one row -- the head variables bound so
+// far, its multiplicity (two words, low first), and per tail the first
+// offset and length of the COLT vector the tail would iterate -- unless a
+// vector is empty.  `handle(t)` gives tail t's entry and `value(v)` the value
+// of variable v.  The element's bag size is added to my_count.  Rows are
+// appended warp-wide: every lane of the warp calls this together.
+template <typename H, typename V>
+__device__ __forceinline__ void factor_emit(const NodeDev& nd, const AtomDev* atoms,
+                                            ResultDev* res, bool live, uint64_t mult,
+                                            H handle, V value,
+                                            unsigned long long& my_count) {
+  uint64_t m = live ? mult : 0;
+  for (int t = 0; t < nd.n_tail && m; ++t) {
+    const TailDev& td = nd.tail[t];
+    m = mul_sat(m, atoms[td.atom].L[td.lvl].count[handle(t)], &res->status);
+  }
+  const bool emit = m != 0;
+  const uint32_t em = __ballot_sync(0xffffffffu, emit);
+  uint64_t base = 0;
+  if (lane_id() == 0 && em) base = atomicAdd(&res->n_out, (unsigned long long)__popc(em));
+  base = __shfl_sync(0xffffffffu, (unsigned long long)base, 0);
+  if (!emit) return;
+  const unsigned long long before = my_count;
+  my_count += m;
+  if (my_count < before) atomicOr(&res->status, kStCountOverflow);
+  const uint64_t pos = base + __popc(em & lanemask_lt());
+  if (pos >= nd.out_rows_cap) {
+    atomicOr(&res->status, kStOutputOverflow);
+    return;
+  }
+  const int width = nd.n_pre + 2 + 2 * nd.n_tail;
+  int32_t* row = nd.out_tuples + pos * uint64_t(width);
+  for (int k = 0; k < nd.n_pre; ++k) row[k] = value(nd.pre_var[k]);
+  row[nd.n_pre] = int32_t(uint32_t(mult));
+  row[nd.n_pre + 1] = int32_t(uint32_t(mult >> 32));
+  for (int t = 0; t < nd.n_tail; ++t) {
+    const TailDev& td = nd.tail[t];
+    const LevelDev& L = atoms[td.atom].L[td.lvl];
+    const uint32_t h = handle(t);
+    row[nd.n_pre + 2 + 2 * t] = int32_t(L.begin[h]);
+    row[nd.n_pre + 3 + 2 * t] = int32_t(L.count[h]);
+  }
+}
+
 // Expansion of one node over positions [chunk_begin, chunk_end): batches of
 // T = R * 256 cover elements; thread t owns batch elements r * 256 + t.  Each
 // probe phase first gathers the keys of all of a thread's live elements,
@@ -454,6 +499,18 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
           }
         }
       }
+    } else if (nd.mode == kModeFactorized) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = r * kThreads + tid;
+        factor_emit(
+            nd, atoms, res, alive >> r & 1u, mult[r],
+            [&](int t) {
+              const TailDev& td = nd.tail[t];
+              return td.hsrc >= 0 ? s_newh[td.hsrc * T + i] : nd.in_h[td.atom][it[r]];
+            },
+            [&](int v) { return load_var(nd, atoms, v, it[r], ch[r], elem[r]); }, my_count);
+      }
     } else {  // kModeMaterialize
       uint64_t tot = 0;
 #pragma unroll
@@ -481,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
   }
   // Block totals.
   __syncthreads();
-  if (nd.mode == kModeAggregate) {
+  if (nd.mode == kModeAggregate || nd.mode == kModeFactorized) {
     unsigned long long tot = block_sum<unsigned long long>(my_count, s_red);
     int any = __syncthreads_or(any_out);
     if (tid == 0 && tot) {
@@ -490,7 +547,8 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
     }
     // Every MIN slot is flushed (a slot still at INT32_MAX leaves the result
     // unchanged); validity of the MINs is COUNT > 0.
-    if (any && tid < FJ_MAX_VARS) atomicMin(&res->mins[tid], s_min[tid]);
+    if (nd.mode == kModeAggregate && any && tid < FJ_MAX_VARS)
+      atomicMin(&res->mins[tid], s_min[tid]);
   }
   unsigned long long v;
   v = block_sum<unsigned long long>(c_iters, s_red);
@@ -846,6 +904,18 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
           }
         }
       }
+    } else if (nd.mode == kModeFactorized) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = slot[r];
+        factor_emit(
+            nd, atoms, res, live >> r & 1u, mult[r],
+            [&](int t) {
+              const TailDev& td = nd.tail[t];
+              return td.hsrc >= 0 ? s_newh[td.hsrc * T + i] : nd.in_h[td.atom][it[r]];
+            },
+            [&](int v) { return src_value(nd.src[v], it[r], elem[r]); }, my_count);
+      }
     } else {  // kModeMaterialize
       uint64_t tot = 0;
 #pragma unroll
@@ -871,14 +941,15 @@ __global__ void __launch_bounds__(kThreads, expand_min_blocks(R))
     }
   }
   __syncthreads();
-  if (nd.mode == kModeAggregate) {
+  if (nd.mode == kModeAggregate || nd.mode == kModeFactorized) {
     unsigned long long tot = block_sum<unsigned long long>(my_count, s_red);
     int any = __syncthreads_or(any_out);
     if (tid == 0 && tot) {
       unsigned long long old = atomicAdd(&res->count, tot);
       if (old + tot < old) atomicOr(&res->status, kStCountOverflow);
     }
-    if (any && tid < FJ_MAX_VARS) atomicMin(&res->mins[tid], s_min[tid]);
+    if (nd.mode == kModeAggregate && any && tid < FJ_MAX_VARS)
+      atomicMin(&res->mins[tid], s_min[tid]);
   }
   unsigned long long v;
   v = block_sum<unsigned long long>(c_iters, s_red);

@@ -461,6 +461,13 @@ __device__ __forceinline__ void scan_epilogue(const NodeDev& nd, const ScanDev& 
         }
       }
     }
+  } else if (nd.mode == kModeFactorized) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      factor_emit(
+          nd, atoms, res, live >> r & 1u, mult[r],
+          [&](int t) { return scan_handle(sc, b, nd.tail[t].hsrc, idx[r]); },
+          [&](int v) { return src_value(nd.src[v], 0, row[r]); }, my_count);
   } else {  // kModeMaterialize
     uint64_t tot = 0;
 #pragma unroll
@@ -494,14 +501,14 @@ __device__ __forceinline__ void scan_block_totals(const NodeDev& nd, ResultDev* 
                                                   unsigned long long surv,
                                                   unsigned long long c_probe,
                                                   unsigned long long c_hit) {
-  if (nd.mode == kModeAggregate) {
+  if (nd.mode == kModeAggregate || nd.mode == kModeFactorized) {
     unsigned long long tot = block_sum<unsigned long long>(my_count, s_red);
     int any_b = __syncthreads_or(any);
     if (threadIdx.x == 0 && tot) {
       unsigned long long old = atomicAdd(&res->count, tot);
       if (old + tot < old) atomicOr(&res->status, kStCountOverflow);
     }
-    if (any_b && threadIdx.x < FJ_MAX_VARS)
+    if (nd.mode == kModeAggregate && any_b && threadIdx.x < FJ_MAX_VARS)
       atomicMin(&res->mins[threadIdx.x], s_min[threadIdx.x]);
   }
   unsigned long long v = block_sum<unsigned long long>(surv, s_red);
@@ -982,12 +989,12 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_con
   if (!__shfl_sync(0xffffffffu, last, 0)) return;
   __threadfence_block();
   const volatile unsigned long long* vt = s_tot;
-  if (nd.mode == kModeAggregate) {
+  if (nd.mode == kModeAggregate || nd.mode == kModeFactorized) {
     if (lane == 0 && vt[0]) {
       const unsigned long long old = atomicAdd(&res->count, vt[0]);
       if (old + vt[0] < old) atomicOr(&res->status, kStCountOverflow);
     }
-    if (vt[4])
+    if (nd.mode == kModeAggregate && vt[4])
       atomicMin(&res->mins[lane], reinterpret_cast<volatile int32_t*>(s_min)[lane]);
   }
   if (lane == 0) {

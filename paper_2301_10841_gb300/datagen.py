@@ -94,9 +94,23 @@ def four_cycle_query(edges):
 # Star join
 # ---------------------------------------------------------------------------
 
+ZIPF_EXACT_MAX = 4_000_000  # larger domains use the continuous inverse CDF
+
+
 def zipf_ranks(n_items, s, size, rng):
     """Ranks in [0, n_items) with P(rank r) proportional to (r+1)^-s, by
-    inverse-CDF lookup on the cumulative weights."""
+    inverse-CDF lookup on the cumulative weights.  Domains above
+    ZIPF_EXACT_MAX items (the chooser's 1M-50M-row evaluation relations) use
+    the inverse of the continuous power law on [1, n_items + 1) instead,
+    floor(x) - 1 with x = (1 + u ((n+1)^(1-s) - 1))^(1/(1-s)) (x = (n+1)^u
+    when s = 1): the same tail exponent without an n-element table."""
+    if n_items > ZIPF_EXACT_MAX:
+        u = rng.random(size)
+        if abs(s - 1.0) < 1e-9:
+            x = np.power(float(n_items + 1), u)
+        else:
+            x = np.power(1.0 + u * ((n_items + 1.0) ** (1.0 - s) - 1.0), 1.0 / (1.0 - s))
+        return np.clip(np.floor(x).astype(np.int64) - 1, 0, n_items - 1)
     w = np.arange(1, n_items + 1, dtype=np.float64) ** (-s)
     cdf = np.cumsum(w)
     cdf /= cdf[-1]

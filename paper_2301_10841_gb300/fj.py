@@ -27,7 +27,7 @@ _lib = ctypes.CDLL(_SO)
 MAX_VARS = 32
 OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 COVER = {"static": 0, "fewest": 1, "learned": 2}
-OUT = {"materialize": 0, "count": 1, "count_min": 2}
+OUT = {"materialize": 0, "count": 1, "count_min": 2, "factorized": 3}
 FLAG_EAGER_ALL = 1
 FLAG_EAGER_ROOT = 2
 FLAG_TIMING = 4
@@ -158,6 +158,9 @@ _sig = {
                             ctypes.c_int),
     "fj_stats_last_error": ([], ctypes.c_char_p),
     "fj_result_copy_tuples": ([_vp, _P(_Result), _vp, ctypes.c_int], ctypes.c_int),
+    "fj_prepared_factor_layout": ([_vp, _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int),
+                                   _P(ctypes.c_int), _P(ctypes.c_int)], ctypes.c_int),
+    "fj_prepared_expand": ([_vp, _P(_Result), _vp, ctypes.c_uint64], ctypes.c_int),
     "fj_execute_bushy": ([_vp, _P(_Query), _P(_BushyNode), ctypes.c_int, _P(_Opts), _P(_Result)],
                          ctypes.c_int),
     "fj_result_free": ([_vp, _P(_Result)], None),
@@ -393,6 +396,7 @@ class Relation:
 
 class Result:
     def __init__(self, res, tuples, min_vars):
+        self._raw = res
         self.count = int(res.count)
         self.mins = [int(res.mins[i]) if res.min_valid[i] else None for i in range(len(min_vars))]
         self.tuples = tuples
@@ -521,6 +525,8 @@ class Prepared:
         self.ctx = ctx
         self.min_vars = list(min_vars or [])
         self.out_mode = out_mode
+        self._head = list(head) if head is not None else None
+        self._atoms_vars = [list(a["vars"]) for a in atoms]
         # The library borrows the relations' columns: keep them alive.
         self._rels = [a["rel"] for a in atoms]
         q, p = _QueryC(atoms, head), _PlanC(plan)
@@ -536,8 +542,31 @@ class Prepared:
     def execute(self):
         res = _Result()
         _check(_lib.fj_execute_prepared(self.handle, ctypes.byref(res)))
-        tuples = _take_tuples(self.ctx, res, res.n_head) if self.out_mode == "materialize" else None
+        tuples = (_take_tuples(self.ctx, res, res.n_head)
+                  if self.out_mode in ("materialize", "factorized") else None)
         return Result(res, tuples, self.min_vars)
+
+    def factor_layout(self):
+        """fj_prepared_factor_layout: (width, prefix variables, tail atoms)."""
+        w, npre, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        pv = (ctypes.c_int * MAX_VARS)()
+        ta = (ctypes.c_int * 16)()
+        _check(_lib.fj_prepared_factor_layout(self.handle, ctypes.byref(w), ctypes.byref(npre), pv,
+                                              ctypes.byref(nt), ta))
+        return w.value, [pv[i] for i in range(npre.value)], [ta[i] for i in range(nt.value)]
+
+    def expand(self, result):
+        """fj_prepared_expand: the factorized `result` (this plan's last) as
+        flat head-order tuples, an (count, n_head) int32 CUDA tensor."""
+        import torch
+        n_head = len(self._head) if self._head is not None else None
+        raw = result._raw
+        if n_head is None:
+            n_head = len({v for a in self._atoms_vars for v in a})
+        t = torch.empty((result.count, n_head), dtype=torch.int32, device=f"cuda:{self.ctx.device}")
+        _check(_lib.fj_prepared_expand(self.handle, ctypes.byref(raw), _vp(t.data_ptr()),
+                                       result.count))
+        return t
 
     def execute_async(self):
         """Enqueue an execution; :meth:`result` waits for it."""
@@ -546,7 +575,8 @@ class Prepared:
     def result(self):
         res = _Result()
         _check(_lib.fj_prepared_result(self.handle, ctypes.byref(res)))
-        tuples = _take_tuples(self.ctx, res, res.n_head) if self.out_mode == "materialize" else None
+        tuples = (_take_tuples(self.ctx, res, res.n_head)
+                  if self.out_mode in ("materialize", "factorized") else None)
         return Result(res, tuples, self.min_vars)
 
     def reset(self):
