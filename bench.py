@@ -621,7 +621,7 @@ def run_batched(args, rank, world):
             graphed.append(i)
         except fj.FJError:
             single.append(i)
-    batch = fj.Batch(ctx, [tuned[i] for i in graphed], graph=True)
+    batch = fj.Batch(ctx, [tuned[i] for i in graphed], graph=True, concurrent=True)
     flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
@@ -692,7 +692,8 @@ def run_batched(args, rank, world):
                                    f"rows log-uniform in [1e3, {args.max_rows:.0e}], Zipf FKs "
                                    f"s in [0.5, 1.5], selection p2 < 5e8; COUNT + MIN(p1) each",
                        "plan": "factor(binary2fj(order)) per query, autotuned cover-batch "
-                               "size and load factor",
+                               "size and load factor; one CUDA graph with eight concurrent "
+                               "branches",
                        "graphed_queries": len(graphed), "single_queries": len(single),
                        "l2": L2_NOTE, "in_tuples": in_tuples},
             "result": {"out_tuples": out_tuples},
@@ -743,10 +744,10 @@ def run_chooser(args, rank, world):
     rng = np.random.default_rng(0)
     xs, ys = [], []
     for q in range(args.train_queries):
-        atoms, _ = G.chooser_query(q, 2_000, 20_000)
+        atoms, _ = G.chooser_query(q, args.train_min_rows, args.train_max_rows)
         d = device(atoms)
-        for f, w, _ in C.samples(fj, ctx, d, C.training_candidates([a["vars"] for a in atoms],
-                                                                   6, rng)):
+        cands = C.training_candidates([a["vars"] for a in atoms], 4, rng)
+        for f, w, _ in C.samples(fj, ctx, d, cands, label=args.label):
             xs.append(f)
             ys.append(w)
         for a in d:
@@ -816,10 +817,11 @@ def run_chooser(args, rank, world):
                                    f"seeds 2005..): 5-relation snowflakes and 5-cycles, rows "
                                    f"log-uniform in [{args.min_rows}, {args.max_rows}], Zipf "
                                    f"keys s in [0.8, 1.6]; COUNT(*)",
-                       "training": f"{args.train_queries} generated queries of 2K-20K rows, the "
-                                   "declared order and five other connected orders each, both "
-                                   "cover policies, label log2 engine work; 60 epochs on the "
-                                   "library's kernels",
+                       "training": f"{args.train_queries} generated queries of "
+                                   f"{args.train_min_rows}-{args.train_max_rows} rows, the "
+                                   "declared order and three other connected orders each, both "
+                                   f"cover policies, label log2 engine {args.label}; 60 epochs on "
+                                   "the library's kernels",
                        "l2": L2_NOTE, "in_tuples": in_tuples},
             "result": {"out_tuples": out_tuples},
             "policies": {k: {"ms_per_step": v, "value": tot / (v / 1000)} for k, v in ms.items()},
@@ -965,6 +967,9 @@ def main():
                     choices=["star", "rmat-triangle", "batched", "chooser", "ablation"])
     ap.add_argument("--rmat-scale", type=int, default=18)
     ap.add_argument("--train-queries", type=int, default=10_000)
+    ap.add_argument("--train-min-rows", type=int, default=2_000)
+    ap.add_argument("--train-max-rows", type=int, default=20_000)
+    ap.add_argument("--label", default="work", choices=["work", "time"])
     ap.add_argument("--min-rows", type=int, default=50_000)
     ap.add_argument("--n-queries", type=int, default=256)
     ap.add_argument("--max-rows", type=int, default=2_000_000)

@@ -386,6 +386,12 @@ void fj_prepared_free(fj_prepared* prep);
  * run on their own while a batch execution is in flight.  `results` holds n
  * fj_result, filled as fj_prepared_result would fill them. */
 #define FJ_BATCH_GRAPH 1
+#define FJ_BATCH_CONCURRENT 2  /* with FJ_BATCH_GRAPH: the graph holds eight
+                                  independent branches (queries dealt round
+                                  robin), which the GPU runs side by side;
+                                  root levels are then built by the
+                                  multi-launch force instead of the
+                                  cooperative kernel */
 fj_status fj_batch_create(fj_ctx* ctx, int n, fj_prepared* const* preps, int flags,
                           fj_batch** out);
 fj_status fj_batch_execute(fj_batch* batch, fj_result* results);

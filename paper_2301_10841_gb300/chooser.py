@@ -9,7 +9,8 @@ policy of any prepared plan.  This module only marshals data for training:
 
 * a training sample is a candidate of an engine-generated query, labelled
   with log2 of the work the exact engine does on it (cover elements
-  iterated plus probes, from its counters) -- deterministic, unlike a time;
+  iterated plus probes, from its counters; deterministic) or of the device
+  time it takes;
 * the network is trained on standardized features and labels by the
   library's own kernels, and its feature scaler is stored in the model
   (``Model.set_scaler``) so that the library can standardize by itself.
@@ -63,14 +64,37 @@ def work(result):
     return c["cover_iters"] + c["probes"]
 
 
-def samples(fj, ctx, dev_atoms, candidates):
-    """(features, log2 work, count) of each candidate, run by the engine."""
+def samples(fj, ctx, dev_atoms, candidates, label="work", reps=2):
+    """(features, label, count) of each candidate, run by the engine.  The
+    label is log2 of the engine's work (``label="work"``: deterministic) or
+    of its device time in microseconds (``label="time"``: the best of
+    ``reps`` executions from scratch after a warm one, between CUDA events
+    on the context's stream)."""
+    import torch
     feats = fj.plan_features(ctx, dev_atoms, candidates)
     rows = []
+    stream = torch.cuda.current_stream()
     for f, (order, pol) in zip(feats, candidates):
         plan = fj.binary_to_free_plan(dev_atoms, order, factor=True)
-        r = fj.execute(ctx, dev_atoms, plan, out_mode="count", cover=pol)
-        rows.append((f, np.log2(work(r) + 1.0), r.count))
+        if label == "work":
+            r = fj.execute(ctx, dev_atoms, plan, out_mode="count", cover=pol)
+            rows.append((f, np.log2(work(r) + 1.0), r.count))
+            continue
+        prep = fj.Prepared(ctx, dev_atoms, plan, out_mode="count", cover=pol)
+        r = prep.execute()
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            prep.reset()
+            e0.record(stream)
+            prep.execute_async()
+            e1.record(stream)
+            r = prep.result()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        prep.free()
+        rows.append((f, np.log2(best * 1000.0 + 1.0), r.count))
     return rows
 
 

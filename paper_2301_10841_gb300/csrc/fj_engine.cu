@@ -172,6 +172,7 @@ struct fj_prepared {
   int fuse_blocks = 0;  // > 0: node 0 runs as one k_scan_fused launch of this many blocks
   bool device_totals = false;  // node totals stay on the device (batched runs)
   ResultDev* d_res = nullptr;  // this query's result block (device)
+  void* d_partials = nullptr;  // its scan partials (queries of a batch may run concurrently)
   ResultDev* h_res = nullptr;  // and its pinned host copy
   RootsState* roots_state = nullptr;  // k_force_roots barrier
   int roots_grid = 0;                 // > 0: root-only forces run as one cooperative launch
@@ -221,10 +222,10 @@ void run_scan(fj_prepared* P, Op op, int n_jobs, uint64_t ub_n) {
   fj_ctx* c = P->ctx;
   int nb = blocks_for(ub_n, 4096, kScanBlocks);
   dim3 g(nb, n_jobs);
-  k_scan_reduce<T, Op><<<g, kThreads, 0, c->stream>>>(op, static_cast<T*>(c->d_partials));
-  k_scan_mid<T, Op><<<dim3(1, n_jobs), 1024, 0, c->stream>>>(op, static_cast<T*>(c->d_partials),
+  k_scan_reduce<T, Op><<<g, kThreads, 0, c->stream>>>(op, static_cast<T*>(P->d_partials));
+  k_scan_mid<T, Op><<<dim3(1, n_jobs), 1024, 0, c->stream>>>(op, static_cast<T*>(P->d_partials),
                                                              nb);
-  k_scan_down<T, Op><<<g, kThreads, 0, c->stream>>>(op, static_cast<T*>(c->d_partials));
+  k_scan_down<T, Op><<<g, kThreads, 0, c->stream>>>(op, static_cast<T*>(P->d_partials));
   CK_LAUNCH("scan");
   P->kernels += 3;
 }
@@ -1236,6 +1237,7 @@ static fj_prepared* prepare(fj_ctx* ctx, const fj_query* query, const fj_plan* p
   CK(cudaSetDevice(ctx->device));
   try {
     P->d_res = P->alloc<ResultDev>(1);
+    P->d_partials = P->alloc<uint64_t>(size_t(kMaxScanJobs) * kScanBlocks);
     CK(cudaMallocHost(&P->h_res, sizeof(ResultDev)));
     compile(P.get());
     upload_atoms(P.get(), query);
@@ -1285,9 +1287,10 @@ static bool batchable(const fj_prepared* P, std::string* why) {
   return true;
 }
 
-static void batch_enqueue(fj_batch* B) {
+static void batch_enqueue(fj_batch* B, const std::vector<cudaStream_t>* branches = nullptr) {
   for (size_t i = 0; i < B->preps.size(); ++i) {
     fj_prepared* P = B->preps[i];
+    if (branches) B->ctx->stream = (*branches)[i % branches->size()];
     begin_execution(P);
     reset_state(P, true);
     P->device_totals = true;
@@ -1320,32 +1323,91 @@ static fj_batch* batch_create(fj_ctx* ctx, int n, fj_prepared* const* preps, int
   }
   B->kernels.assign(n, 0);
   B->chunks.assign(n, 0);
+  if ((flags & FJ_BATCH_CONCURRENT) && !(flags & FJ_BATCH_GRAPH))
+    fail(FJ_ERR_INVALID_ARG, "FJ_BATCH_CONCURRENT needs FJ_BATCH_GRAPH");
   if (flags & FJ_BATCH_GRAPH) {
     // Capture on a private stream (the context's stream may be the legacy
     // default stream, which cannot be captured); the graph is launched on
-    // the context's stream.
+    // the context's stream.  FJ_BATCH_CONCURRENT: the queries are spread
+    // over kBranches streams forked from it and joined at the end, so the
+    // graph holds independent branches the GPU runs side by side; their
+    // root levels are then built by the multi-launch force (cooperative
+    // launches must not share the GPU), without the per-entry tail MINs.
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->stream));
+    const bool conc = flags & FJ_BATCH_CONCURRENT;
+    constexpr int kBranches = 8;
     cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> evs;
     CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaStream_t saved = ctx->stream;
+    struct Saved {
+      int roots_grid;
+      std::vector<const int32_t*> tmin;
+    };
+    std::vector<Saved> keep;
+    auto restore = [&] {
+      ctx->stream = saved;
+      for (size_t i = 0; i < keep.size(); ++i) {
+        fj_prepared* P = B->preps[i];
+        P->roots_grid = keep[i].roots_grid;
+        for (size_t t = 0; t < keep[i].tmin.size(); ++t) P->nd[P->last].tail[t].tmin = keep[i].tmin[t];
+      }
+      for (cudaStream_t b : br) cudaStreamDestroy(b);
+      for (cudaEvent_t e : evs) cudaEventDestroy(e);
+      cudaStreamDestroy(cap);
+    };
+    if (conc) {
+      for (fj_prepared* P : B->preps) {
+        Saved sv{P->roots_grid, {}};
+        if (P->last >= 0)
+          for (int t = 0; t < P->nd[P->last].n_tail; ++t) {
+            sv.tmin.push_back(P->nd[P->last].tail[t].tmin);
+            P->nd[P->last].tail[t].tmin = nullptr;
+          }
+        P->roots_grid = 0;
+        keep.push_back(sv);
+      }
+      for (int i = 0; i < kBranches; ++i) {
+        cudaStream_t b = nullptr;
+        cudaEvent_t e = nullptr;
+        CK(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+        br.push_back(b);
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        evs.push_back(e);
+      }
+      cudaEvent_t e = nullptr;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      evs.push_back(e);
+    }
     ctx->stream = cap;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       try {
-        batch_enqueue(B.get());
+        if (conc) {
+          cudaEvent_t fork = evs[kBranches];
+          CK(cudaEventRecord(fork, cap));
+          for (cudaStream_t b : br) CK(cudaStreamWaitEvent(b, fork, 0));
+          batch_enqueue(B.get(), &br);
+          for (int i = 0; i < kBranches; ++i) {
+            CK(cudaEventRecord(evs[i], br[i]));
+            CK(cudaStreamWaitEvent(cap, evs[i], 0));
+          }
+        } else {
+          batch_enqueue(B.get());
+        }
       } catch (...) {
         cudaGraph_t g = nullptr;
+        ctx->stream = cap;
         cudaStreamEndCapture(cap, &g);
         if (g) cudaGraphDestroy(g);
-        ctx->stream = saved;
-        cudaStreamDestroy(cap);
+        restore();
         throw;
       }
       e = cudaStreamEndCapture(cap, &B->graph);
     }
-    ctx->stream = saved;
-    cudaStreamDestroy(cap);
+    restore();
     CK(e);
     CK(cudaGraphInstantiate(&B->exec, B->graph, 0));
   }

@@ -731,8 +731,8 @@ __global__ void k_force_reset_req(ForceJobs fj) {
 constexpr int kRootThreads = 512;
 
 struct RootsState {        // zero at the start of each execution (k_reset)
-  unsigned int bar_count;  // blocks arrived at the current barrier (back to 0 after each)
-  unsigned int bar_gen;    // barriers completed
+  unsigned int bar_count;  // block arrivals at grid barriers this execution
+  unsigned int bar_gen;    // grid barriers completed this execution
   // Per job: rows passing, keys.  Launches alternate between the two sets;
   // a launch zeroes the set the next launch uses.
   unsigned int n_pass[2][FJ_MAX_ATOMS];
@@ -741,35 +741,45 @@ struct RootsState {        // zero at the start of each execution (k_reset)
 
 constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about a second)
 
-// Grid-wide barrier among all blocks of a cooperative launch.  Returns false
-// (in every thread of the block) when the wait ran out.
-// `extra` blocks more than the grid are awaited (a test of the bounded
-// wait: with extra > 0 the barrier never completes).
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier among all blocks of a cooperative launch.  The arrival
+// counter and the generation only grow (k_reset zeroes both at the start of
+// an execution, so between barriers count = generation x grid): the block
+// that completes barrier number `target` (generations since the execution
+// began, counted by the caller) publishes it with one release store, and the
+// others poll it with acquire loads -- the arrival's release and the poll's
+// acquire order the blocks' writes around the barrier.  Returns false (in
+// every thread of the block) when the wait ran out; `never` (the test of
+// the bounded wait) makes the barrier wait for an arrival that never comes.
 __device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status, uint32_t spin,
-                                          uint32_t extra = 0) {
+                                          uint32_t target, bool never = false) {
   const uint32_t limit = spin ? spin : kGridSpinLimit;
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &cs->bar_gen;
-    const unsigned int gen = *vgen;
-    __threadfence();
-    if (atomicAdd(&cs->bar_count, 1u) == gridDim.x + extra - 1) {
-      cs->bar_count = 0;
-      __threadfence();
-      atomicAdd(&cs->bar_gen, 1u);
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;"
+                 : "=r"(old)
+                 : "l"(&cs->bar_count)
+                 : "memory");
+    if (!never && old == target * gridDim.x - 1) {
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&cs->bar_gen), "r"(target)
+                   : "memory");
     } else {
       uint32_t it = 0;
-      while (*vgen == gen) {
+      while (ld_acquire_gpu(&cs->bar_gen) < target) {
         if (++it > limit) {
           atomicOr(status, kStTimeout);
           ok = 0;
           break;
         }
-        __nanosleep(32);
       }
     }
-    __threadfence();
   }
   return __syncthreads_and(ok);
 }
@@ -912,6 +922,9 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   __shared__ uint32_t s_scan[33];
   __shared__ unsigned long long s_scan64[33];
   __shared__ uint32_t s_base, s_base2;
+  // Grid barriers completed before this launch (an execution may launch the
+  // build more than once); only thread 0 takes part in the barriers.
+  uint32_t bar_target = tid == 0 ? ld_acquire_gpu(&cs->bar_gen) : 0u;
   if (tid < uint32_t(nj)) {
     const int2 jb = fj.jobs[tid];
     const AtomDev& a = fj.atoms[jb.x];
@@ -1012,7 +1025,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     const int j = job_at(s_off, nj, x);
     reinterpret_cast<uint4*>(s_job[j].filter)[x - s_off[j]] = make_uint4(0u, 0u, 0u, 0u);
   }
-  if (!grid_sync(cs, &res->status, spin, test_timeout ? 1u : 0u)) return;
+  if (!grid_sync(cs, &res->status, spin, ++bar_target, test_timeout != 0)) return;
   if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[set][tid];
   __syncthreads();
 
@@ -1049,7 +1062,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     // until D (one word per slot: every second uint4 of a wide table).
     if (J.tmin && (!J.wide || !(u & 1u))) J.sbegin[J.wide ? u / 2 : u] = uint32_t(INT32_MAX);
   }
-  if (!grid_sync(cs, &res->status, spin)) return;
+  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
 
   // C: insert every passing row's key (E per thread, their first
   // compare-and-swaps in flight together) and count rows per key.
@@ -1134,7 +1147,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       }
     }
   }
-  if (!grid_sync(cs, &res->status, spin)) return;
+  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
 
   // D: the occupied slots of each table (a slot is occupied once a row has
   // been counted in it) become the root's entries, in slot order, each with
@@ -1206,7 +1219,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       __syncthreads();
     }
   }
-  if (!grid_sync(cs, &res->status, spin)) return;
+  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
   if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[set][tid];
   __syncthreads();
 

@@ -597,14 +597,17 @@ class Prepared:
 class Batch:
     """fj_batch_create / fj_batch_execute: prepared queries run back to back
     from scratch with one synchronization; ``graph=True`` captures them once
-    into a CUDA graph (FJ_BATCH_GRAPH) so each execution is one launch."""
+    into a CUDA graph (FJ_BATCH_GRAPH) so each execution is one launch;
+    ``concurrent=True`` (FJ_BATCH_CONCURRENT) spreads them over independent
+    branches of the graph."""
 
-    def __init__(self, ctx, preps, graph=False):
+    def __init__(self, ctx, preps, graph=False, concurrent=False):
         self.ctx = ctx
         self.preps = list(preps)
         arr = (_vp * max(1, len(self.preps)))(*[p.handle for p in self.preps])
         self.handle = _vp()
-        _check(_lib.fj_batch_create(ctx.handle, len(self.preps), arr, 1 if graph else 0,
+        flags = (1 if graph else 0) | (2 if concurrent else 0)
+        _check(_lib.fj_batch_create(ctx.handle, len(self.preps), arr, flags,
                                     ctypes.byref(self.handle)))
         ctx._adopt(self)
 

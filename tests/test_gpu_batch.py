@@ -1,6 +1,7 @@
 """Batches of independent PK-FK chain and star queries (fj_batch_*): every
 query's COUNT and MINs equal the oracle's hash join of the same query, run
-eagerly and as one captured CUDA graph (replayed twice); a query whose
+eagerly, as one captured CUDA graph and as one graph of concurrent branches
+(each replayed twice); a query whose
 output size the host would decide (materialized output) is refused with
 FJ_ERR_UNSUPPORTED."""
 
@@ -23,15 +24,20 @@ def test_batch_matches_oracle(fj, ctx):
         plan = fj.binary_to_free_plan(dev, order, factor=True)
         preps.append(fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins))
     assert len(preps) == 48
-    for graph in (False, True):
-        b = fj.Batch(ctx, preps, graph=graph)
+    for graph, conc in ((False, False), (True, False), (True, True)):
+        b = fj.Batch(ctx, preps, graph=graph, concurrent=conc)
         for _ in range(2):
             got = [(r.count, r.mins) for r in b.execute()]
-            assert got == want
+            assert got == want, (graph, conc)
         b.free()
-    # A prepared query still runs on its own after the batches.
-    r = preps[0].execute()
-    assert (r.count, r.mins) == want[0]
+    # A prepared query still runs on its own after the batches (the
+    # concurrent capture's settings are put back).
+    for p, w in zip(preps[:4], want[:4]):
+        p.reset()
+        r = p.execute()
+        assert (r.count, r.mins) == w
+    with pytest.raises(fj.FJError):
+        fj.Batch(ctx, preps, graph=False, concurrent=True)
 
 
 def test_batch_refuses_host_decisions(fj, ctx):

@@ -109,12 +109,13 @@ def test_batched_workload_real_sizes(fj, ctx):
         bs, lf = cfgs[i % len(cfgs)]
         preps.append(fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins,
                                  batch_size=bs, load_factor=lf))
-    batch = fj.Batch(ctx, preps, graph=True)
-    for _ in range(2):
-        res = batch.execute()
-        for q, r, w in zip(picks, res, wants):
-            assert (r.count, r.mins) == w, q
-    batch.free()
+    for conc in (False, True):
+        batch = fj.Batch(ctx, preps, graph=True, concurrent=conc)
+        for _ in range(2):
+            res = batch.execute()
+            for q, r, w in zip(picks, res, wants):
+                assert (r.count, r.mins) == w, (q, conc)
+        batch.free()
     for p, w in zip(preps, wants):
         p.reset()
         r = p.execute()
