@@ -738,8 +738,8 @@ def run_chooser(args, rank, world):
         return [{"rel": ctx.relation([torch.from_numpy(c).to(dev) for c in a["cols"]]),
                  "vars": a["vars"]} for a in atoms]
 
-    # Training: engine-generated queries, six orders x two cover policies
-    # each, labelled with the engine's work (untimed).
+    # Pretraining: small engine-generated queries, four orders x two cover
+    # policies each, labelled with the engine's work (untimed).
     t_train = time.perf_counter()
     rng = np.random.default_rng(0)
     xs, ys = [], []
@@ -752,7 +752,34 @@ def run_chooser(args, rank, world):
             ys.append(w)
         for a in d:
             a["rel"].release()
-    model, losses = C.fit(fj, ctx, np.stack(xs), np.asarray(ys, dtype=np.float32))
+    # Fine-tuning: queries composed from a pool of relations at the held-out
+    # scale (their own seeds and relations), six orders x two policies each,
+    # labelled with the device time.
+    xt, yt = [], []
+    t_pool = 0.0
+    if args.tune_queries:
+        t0 = time.perf_counter()
+        pool = G.chooser_pool(args.pool_size, args.pool_min_rows, args.pool_max_rows)
+        dpool = {r["name"]: ctx.relation([torch.from_numpy(c).to(dev) for c in r["cols"]])
+                 for r in pool}
+        t_pool = time.perf_counter() - t0
+        for q in range(args.tune_queries):
+            atoms, _ = G.pool_query(pool, q)
+            d = [{"rel": dpool[a["rel"]["name"]], "vars": a["vars"], "rel_cols": a["rel_cols"]}
+                 for a in atoms]
+            cands = C.training_candidates([a["vars"] for a in atoms], 6, rng)
+            for f, t, _ in C.samples(fj, ctx, d, cands, label="time"):
+                xt.append(f)
+                yt.append(t)
+        for r in dpool.values():
+            r.release()
+    if xs:
+        model, losses = C.fit(fj, ctx, np.stack(xs), np.asarray(ys, dtype=np.float32),
+                              scaler_rows=np.stack(xs + xt))
+        if xt:
+            losses += C.finetune(model, np.stack(xt), np.asarray(yt, dtype=np.float32))
+    else:
+        model, losses = C.fit(fj, ctx, np.stack(xt), np.asarray(yt, dtype=np.float32))
     t_train = time.perf_counter() - t_train
 
     # Held-out queries: the plain converted binary plan, the same plan with
@@ -806,6 +833,25 @@ def run_chooser(args, rank, world):
             times.append(e0.elapsed_time(e1))
         ms[name] = sum(times) / len(times)
     clk = clocks.stop()
+    # Each query alone (best of three, L2 flushed before each), per policy.
+    per_query = {name: [] for name in policies}
+    for name, preps in policies.items():
+        for p in preps:
+            best = None
+            for _ in range(3):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p.reset()
+                p.execute_async()
+                e1.record(stream)
+                p.result()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            per_query[name].append(round(best, 3))
     if rank != 0:
         return
     tot = in_tuples + out_tuples
@@ -817,18 +863,26 @@ def run_chooser(args, rank, world):
                                    f"seeds 2005..): 5-relation snowflakes and 5-cycles, rows "
                                    f"log-uniform in [{args.min_rows}, {args.max_rows}], Zipf "
                                    f"keys s in [0.8, 1.6]; COUNT(*)",
-                       "training": f"{args.train_queries} generated queries of "
+                       "training": f"pretraining: {args.train_queries} generated queries of "
                                    f"{args.train_min_rows}-{args.train_max_rows} rows, the "
                                    "declared order and three other connected orders each, both "
-                                   f"cover policies, label log2 engine {args.label}; 60 epochs on "
-                                   "the library's kernels",
+                                   f"cover policies, label log2 engine {args.label}, 60 epochs; "
+                                   f"fine-tuning: {args.tune_queries} snowflakes and 5-cycles "
+                                   f"over a pool of {args.pool_size} relations of "
+                                   f"{args.pool_min_rows}-{args.pool_max_rows} rows "
+                                   "(datagen.chooser_pool/pool_query, other seeds than the "
+                                   "held-out queries), the declared order and five others, both "
+                                   "policies, label log2 device time, 40 epochs; all on the "
+                                   "library's kernels",
                        "l2": L2_NOTE, "in_tuples": in_tuples},
             "result": {"out_tuples": out_tuples},
             "policies": {k: {"ms_per_step": v, "value": tot / (v / 1000)} for k, v in ms.items()},
             "speedup_vs_plain": ms["plain"] / ms["learned"],
             "speedup_vs_fewest": ms["fewest"] / ms["learned"],
             "choices": choices,
-            "train": {"seconds": t_train, "samples": len(ys), "loss_first": losses[0],
+            "per_query_ms": per_query,
+            "train": {"seconds": t_train, "pool_seconds": t_pool, "samples": len(ys),
+                      "tune_samples": len(yt), "loss_first": losses[0],
                       "loss_last": losses[-1]},
             "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
             "gpu_launches": None, "impl": "fj"}
@@ -970,6 +1024,10 @@ def main():
     ap.add_argument("--train-min-rows", type=int, default=2_000)
     ap.add_argument("--train-max-rows", type=int, default=20_000)
     ap.add_argument("--label", default="work", choices=["work", "time"])
+    ap.add_argument("--tune-queries", type=int, default=400)
+    ap.add_argument("--pool-size", type=int, default=48)
+    ap.add_argument("--pool-min-rows", type=int, default=1_000_000)
+    ap.add_argument("--pool-max-rows", type=int, default=16_000_000)
     ap.add_argument("--min-rows", type=int, default=50_000)
     ap.add_argument("--n-queries", type=int, default=256)
     ap.add_argument("--max-rows", type=int, default=2_000_000)

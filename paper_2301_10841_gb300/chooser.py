@@ -11,6 +11,10 @@ policy of any prepared plan.  This module only marshals data for training:
   with log2 of the work the exact engine does on it (cover elements
   iterated plus probes, from its counters; deterministic) or of the device
   time it takes;
+* the network is pretrained on many small work-labelled queries and then
+  fine-tuned on time-labelled queries at the scale it is used on (work is
+  a poor proxy for time there: the candidate with the least work is often
+  no faster than the declared plan);
 * the network is trained on standardized features and labels by the
   library's own kernels, and its feature scaler is stored in the model
   (``Model.set_scaler``) so that the library can standardize by itself.
@@ -125,18 +129,38 @@ def train(model, x, y, epochs=60, lr=0.03, batch=256, seed=0):
     return losses
 
 
-def fit(fj, ctx, x, y, h1=128, h2=64, epochs=60, lr=0.03, seed=1):
-    """A model trained on (features, log2 work) rows, with its feature
+def fit(fj, ctx, x, y, h1=128, h2=64, epochs=60, lr=0.03, seed=1, scaler_rows=None):
+    """A model trained on (features, log2 cost) rows, with its feature
     scaler set (the library standardizes features itself when it chooses);
     the labels are standardized for training -- the argmin does not depend
-    on that affine map.  Returns (model, losses)."""
+    on that affine map.  The scaler is fitted on ``scaler_rows`` when given
+    (every row the model will see, fine-tuning rows included: a feature
+    that never varies in the first rows would otherwise blow up later),
+    else on x.  Returns (model, losses); the scaler is also kept on the
+    model object (``model.scaler``) for fine-tuning."""
     import torch
     x = np.asarray(x, dtype=np.float32)
     y = np.asarray(y, dtype=np.float32)
-    mean, scale = x.mean(axis=0), x.std(axis=0) + 1e-3
+    xr = x if scaler_rows is None else np.asarray(scaler_rows, dtype=np.float32)
+    mean, scale = xr.mean(axis=0), xr.std(axis=0) + 1e-3
     model = fj.Model(ctx, x.shape[1], h1, h2, max_batch=8192)
     model.set_params(init_params(x.shape[1], h1, h2, seed=seed))
     model.set_scaler(mean, scale)
+    model.scaler = (mean, scale)
     xs = torch.from_numpy(((x - mean) / scale).astype(np.float32)).cuda()
     ys = torch.from_numpy(((y - y.mean()) / (y.std() + 1e-6)).astype(np.float32)).cuda()
     return model, train(model, xs, ys, epochs=epochs, lr=lr)
+
+
+def finetune(model, x, y, epochs=40, lr=0.01):
+    """Continue training a fitted model on new (features, log2 cost) rows --
+    the time-labelled queries at the scale the chooser is used on -- under
+    its existing feature scaler, with the new labels standardized on their
+    own.  Returns the loss curve."""
+    import torch
+    mean, scale = model.scaler
+    x = np.asarray(x, dtype=np.float32)
+    y = np.asarray(y, dtype=np.float32)
+    xs = torch.from_numpy(((x - mean) / scale).astype(np.float32)).cuda()
+    ys = torch.from_numpy(((y - y.mean()) / (y.std() + 1e-6)).astype(np.float32)).cuda()
+    return train(model, xs, ys, epochs=epochs, lr=lr, batch=128)

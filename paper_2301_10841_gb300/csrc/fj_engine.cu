@@ -568,7 +568,13 @@ static void compile(fj_prepared* P) {
       L.key = P->alloc<uint64_t>(n);
       L.ht_cap_max = pow2_at_least(uint64_t(double(n) / load) + 1);
       L.ht = P->alloc<uint4>((size_t(L.ht_cap_max) + 1) * (L.wide ? 2 : 1));
-      if (l == 1) L.sbegin = P->alloc<uint32_t>(size_t(L.ht_cap_max) + 1);
+      if (l == 1) {
+        L.sbegin = P->alloc<uint32_t>(size_t(L.ht_cap_max) + 1);
+        L.slot_of = P->alloc<uint32_t>(n);
+      }
+      L.ht_state = kHtUnknown;  // fresh memory: the first build clears it all
+      L.n_listed = 0;
+      L.used_hi = L.ht_cap_max + 1;
       if (!L.wide) {
         // Bloom filter: about 8 bits per row, 256 B to 32 KB.
         uint32_t words = 64;

@@ -37,6 +37,10 @@ constexpr uint32_t kStItemsOverflow = 1u << 3;
 constexpr uint32_t kStTimeout = 1u << 4;
 constexpr uint32_t kStDrainTimeout = 1u << 5;  // after a timeout, copies in flight did not land
 
+// States of a level's hash table between executions (LevelDev::ht_state).
+constexpr uint32_t kHtListed = 1;
+constexpr uint32_t kHtUnknown = 2;
+
 struct LevelDev {
   // Entries of this level.
   uint32_t* begin = nullptr;
@@ -54,6 +58,10 @@ struct LevelDev {
   // Root levels: per slot, the first offset of its entry's range (written
   // by the root build, read by its scatter).
   uint32_t* sbegin = nullptr;
+  // Root levels: per entry, its slot.  The root build leaves its table
+  // dirty and lists the slots it used here, so that the next build clears
+  // only those instead of the whole table (ht_state below).
+  uint32_t* slot_of = nullptr;
   // Root levels whose entries' vectors a plan folds into COUNT/MIN as a
   // trailing node (a tail): per entry, the MIN of column `tmin_col` over the
   // entry's vector, computed by the root build (a partial aggregate of the
@@ -91,6 +99,14 @@ struct LevelDev {
   uint32_t n_in;       // rows that reach this level's table (sizing)
   uint32_t filter_on;  // the filter is built and selective
   uint32_t n_tmp;      // (row, slot) pairs staged by the current force
+  // State of the table between executions (kept across resets):
+  // kHtListed: empty except the slots slot_of[0, n_listed) (and, for a
+  // tail level, sbegin is INT32_MAX except there); kHtUnknown: any slot
+  // below used_hi may be dirty.
+  uint32_t ht_state = kHtUnknown;
+  uint32_t n_listed = 0;
+  uint32_t used_hi = 0;  // slots [0, used_hi) may have been written
+  uint32_t last_slots = 0;  // slots the last root build's table spanned
 };
 
 struct AtomDev {

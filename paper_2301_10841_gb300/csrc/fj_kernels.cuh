@@ -236,6 +236,20 @@ __device__ __forceinline__ uint32_t* slot_e(uint4* ht, int wide, uint32_t s) {
 __device__ __forceinline__ uint32_t* slot_cnt(uint4* ht, int wide, uint32_t s) {
   return wide ? &ht[2 * size_t(s) + 1].y : &ht[s].w;
 }
+// The root build keeps the row that claimed a slot here until the slot's
+// entry is assigned (a narrow slot's entry field; a wide slot's spare word).
+__device__ __forceinline__ uint32_t* slot_row(uint4* ht, int wide, uint32_t s) {
+  return wide ? &ht[2 * size_t(s) + 1].z : &ht[s].z;
+}
+// Empty a slot.
+__device__ __forceinline__ void slot_clear(uint4* ht, int wide, uint32_t s) {
+  if (wide) {
+    ht[2 * size_t(s)] = make_uint4(kNone, kNone, kNone, kNone);
+    ht[2 * size_t(s) + 1] = make_uint4(kNone, 0u, 0u, 0u);
+  } else {
+    ht[s] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Block-level helpers.
@@ -403,6 +417,9 @@ __global__ void k_force_prepare(ForceJobs fj) {
   uint32_t cap = 16;
   while (float(cap) < want && cap < L.ht_cap_max) cap <<= 1;
   L.mask = cap - 1;
+  // This build leaves no list of the slots it writes.
+  L.ht_state = kHtUnknown;
+  L.used_hi = max(L.used_hi, cap + 1);
   // Keep the filter only with at least 4 bits per key.
   L.filter_on = L.filter && uint64_t(L.n_in) * 4 <= uint64_t(L.filter_words) * 32;
 }
@@ -733,13 +750,21 @@ constexpr int kRootThreads = 512;
 struct RootsState {        // zero at the start of each execution (k_reset)
   unsigned int bar_count;  // block arrivals at grid barriers this execution
   unsigned int bar_gen;    // grid barriers completed this execution
-  // Per job: rows passing, keys.  Launches alternate between the two sets;
-  // a launch zeroes the set the next launch uses.
+  // Per job: rows passing, keys; per launch: some key has more than one
+  // row.  Launches alternate between the two sets; a launch zeroes the set
+  // the next launch uses.
   unsigned int n_pass[2][FJ_MAX_ATOMS];
   unsigned int n_new[2][FJ_MAX_ATOMS];
+  unsigned int dup[2];
 };
 
 constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about a second)
+
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+constexpr uint32_t kPrefetchChunk = 16384;
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   unsigned int v;
@@ -829,6 +854,11 @@ struct RootJob {
   uint32_t* tmp_slot;
   uint32_t* newslots;  // the root build keeps each passing row's rank here
   uint32_t* sbegin;    // per slot: its entry's first offset
+  uint32_t* slot_of;   // per entry: its slot (the list the next build clears)
+  uint32_t state;      // the table's state when the launch began (LevelDev::ht_state)
+  uint32_t n_listed;   // ... and its listed slots
+  uint32_t used_hi;
+  uint32_t last_slots;
   int32_t* tmin;       // per entry: MIN of tcol over its rows (or null)
   const int32_t* tcol;
   uint32_t* perm;
@@ -948,6 +978,11 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     J.tmp_slot = a.tmp_slot;
     J.newslots = a.newslots;
     J.sbegin = L.sbegin;
+    J.slot_of = L.slot_of;
+    J.state = L.slot_of ? L.ht_state : kHtUnknown;
+    J.n_listed = L.n_listed;
+    J.used_hi = L.used_hi;
+    J.last_slots = L.last_slots;
     J.tmin = L.tmin;
     J.tcol = L.tmin ? a.cols[L.tmin_col] : nullptr;
     J.perm = a.perm;
@@ -970,6 +1005,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   if (blockIdx.x == 0 && tid < uint32_t(FJ_MAX_ATOMS)) {
     cs->n_pass[set ^ 1][tid] = 0;
     cs->n_new[set ^ 1][tid] = 0;
+    if (tid == 0) cs->dup[set ^ 1] = 0;
   }
   uint32_t lo, hi;
 
@@ -1025,11 +1061,54 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     const int j = job_at(s_off, nj, x);
     reinterpret_cast<uint4*>(s_job[j].filter)[x - s_off[j]] = make_uint4(0u, 0u, 0u, 0u);
   }
+  // The slots the previous build of a table listed back to empty (and a
+  // tail level's running MINs back to INT32_MAX): the rest of the table is
+  // empty already.  The table's span at the previous build (the same query
+  // spans the same slots again) is prefetched into L2 by bulk copies, so
+  // that the inserts and D meet it there.
+  jobs_prefix(nj, s_off, [&](int j) {
+    const RootJob& J = s_job[j];
+    if (!J.act || J.state != kHtListed) return 0u;
+    const uint32_t tb = J.last_slots * (J.wide ? 32u : 16u);
+    const uint32_t mb = J.tmin ? (J.last_slots * 4u) & ~15u : 0u;  // whole 16-byte units
+    return (tb + kPrefetchChunk - 1) / kPrefetchChunk + (mb + kPrefetchChunk - 1) / kPrefetchChunk;
+  });
+  // Chunk x goes to block x mod grid: the bulk copies of one block are
+  // served one after another.
+  for (uint32_t x = blockIdx.x + gridDim.x * tid; x < s_off[nj]; x += gridDim.x * NT) {
+    const int j = job_at(s_off, nj, x);
+    const RootJob& J = s_job[j];
+    const uint32_t tb = J.last_slots * (J.wide ? 32u : 16u);  // table bytes
+    const uint32_t nt = (tb + kPrefetchChunk - 1) / kPrefetchChunk;
+    const uint32_t c = x - s_off[j];
+    if (c < nt) {
+      const uint32_t off = c * kPrefetchChunk;
+      prefetch_l2(reinterpret_cast<const char*>(J.ht) + off, min(kPrefetchChunk, tb - off));
+    } else {  // then the running MINs
+      const uint32_t off = (c - nt) * kPrefetchChunk;
+      const uint32_t mb = (J.last_slots * 4u) & ~15u;
+      prefetch_l2(reinterpret_cast<const char*>(J.sbegin) + off, min(kPrefetchChunk, mb - off));
+    }
+  }
+  jobs_prefix(nj, s_off, [&](int j) {
+    const RootJob& J = s_job[j];
+    return J.act && J.state == kHtListed ? J.n_listed : 0u;
+  });
+  for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
+    const int j = job_at(s_off, nj, x);
+    const RootJob& J = s_job[j];
+    const uint32_t sl = J.slot_of[x - s_off[j]];
+    slot_clear(J.ht, J.wide, sl);
+    if (J.tmin) J.sbegin[sl] = uint32_t(INT32_MAX);
+  }
   if (!grid_sync(cs, &res->status, spin, ++bar_target, test_timeout != 0)) return;
   if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[set][tid];
   __syncthreads();
 
-  // B: size each table for its passing rows and clear it.
+  // Size each table for its passing rows.  From here on a failed launch
+  // leaves the table in an unknown state; a complete one lists its slots.
+  bool full_clear = false;  // some table is in an unknown state: B clears it
+  for (int j = 0; j < nj; ++j) full_clear |= s_job[j].act && s_job[j].state != kHtListed;
   if (tid < uint32_t(nj)) {
     const RootJob& J = s_job[tid];
     const uint32_t n_in = s_np[tid];
@@ -1043,31 +1122,44 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       L.mask = cap - 1;
       L.filter_on = s_fon[tid];
       L.n_in = n_in;
+      L.ht_state = kHtUnknown;
+      L.used_hi = max(J.used_hi, cap + 1);
     }
   }
-  jobs_prefix(nj, s_off, [&](int j) {
-    const RootJob& J = s_job[j];
-    if (!J.act) return 0u;
-    return (s_mask[j] + 2) * (J.wide ? 2u : 1u);
-  });
-  for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
-    const int j = job_at(s_off, nj, x);
-    const RootJob& J = s_job[j];
-    const uint32_t u = x - s_off[j];
-    if (J.wide)
-      J.ht[u] = (u & 1u) ? make_uint4(kNone, 0u, 0u, 0u) : make_uint4(kNone, kNone, kNone, kNone);
-    else
-      J.ht[u] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
-    // A tail level: sbegin holds each slot's running MIN of the tail column
-    // until D (one word per slot: every second uint4 of a wide table).
-    if (J.tmin && (!J.wide || !(u & 1u))) J.sbegin[J.wide ? u / 2 : u] = uint32_t(INT32_MAX);
+  __syncthreads();
+
+  // B (only after a build that left no list, or the first): clear every
+  // slot of such a table that may have been written.
+  if (full_clear) {
+    jobs_prefix(nj, s_off, [&](int j) {
+      const RootJob& J = s_job[j];
+      if (!J.act || J.state == kHtListed) return 0u;
+      return max(J.used_hi, s_mask[j] + 2) * (J.wide ? 2u : 1u);
+    });
+    for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
+      const int j = job_at(s_off, nj, x);
+      const RootJob& J = s_job[j];
+      const uint32_t u = x - s_off[j];
+      if (J.wide)
+        J.ht[u] = (u & 1u) ? make_uint4(kNone, 0u, 0u, 0u) : make_uint4(kNone, kNone, kNone, kNone);
+      else
+        J.ht[u] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
+      // A tail level: sbegin holds each slot's running MIN of the tail
+      // column until D (one word per slot: every second uint4 of a wide
+      // table).
+      if (J.tmin && (!J.wide || !(u & 1u))) J.sbegin[J.wide ? u / 2 : u] = uint32_t(INT32_MAX);
+    }
+    if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
   }
-  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
 
   // C: insert every passing row's key (E per thread, their first
-  // compare-and-swaps in flight together) and count rows per key.
+  // compare-and-swaps in flight together) and count rows per key.  The
+  // key's first row (rank 0) leaves itself in the slot: D places it when it
+  // is the key's only row, and a tail level's MIN starts from its value
+  // (the other rows fold theirs into the slot's running MIN).
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
   block_range(s_off[nj], lo, hi);
+  bool dup = false;  // some key of this block's rows has another row before it
   for (int j = 0; j < nj; ++j) {
     const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
     if (a0 >= a1) continue;
@@ -1075,12 +1167,11 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     const uint32_t mask = s_mask[j];
     for (uint32_t r = a0 - s_off[j]; r < a1 - s_off[j]; r += E * NT) {
       const uint32_t r1 = a1 - s_off[j];
-      uint32_t slot[E];
-      int32_t tv[E];  // a tail level: each row's value of the tail column
+      uint32_t slot[E], rw[E], clm = 0;  // clm: bit u, row u claimed its slot
 #pragma unroll
       for (int u = 0; u < E; ++u) {
         const uint32_t i = r + u * NT + tid;
-        tv[u] = (J.tmin && i < r1) ? __ldg(J.tcol + J.tmp_row[i]) : 0;
+        rw[u] = i < r1 ? J.tmp_row[i] : 0u;
       }
       if (!J.wide) {
         uint64_t kw[E];
@@ -1094,7 +1185,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
           if (J.nk == 1) {
             kw[u] = J.tmp_slot[i];
           } else {
-            const uint32_t row = J.tmp_row[i];
+            const uint32_t row = rw[u];
             kw[u] = pack_key(0u, J.nk, J.nk > 0 ? __ldg(J.kc[0] + row) : 0,
                              J.nk > 1 ? __ldg(J.kc[1] + row) : 0);
           }
@@ -1116,9 +1207,12 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
             slot[u] = ht_insert(J.ht, mask, kw[u], cl, &res->status);
           else
             slot[u] = ht_insert_from(J.ht, mask, kw[u], h[u], old[u], cl, &res->status);
-          if (cl && s_fon[j]) {
-            const uint32_t fh = filter_hash(kw[u]);
-            atomicOr(&J.filter[fh & (J.filter_words - 1)], bloom_bits(fh));
+          if (cl) {
+            clm |= 1u << u;
+            if (s_fon[j]) {
+              const uint32_t fh = filter_hash(kw[u]);
+              atomicOr(&J.filter[fh & (J.filter_words - 1)], bloom_bits(fh));
+            }
           }
         }
       } else {
@@ -1127,106 +1221,56 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
           const uint32_t i = r + u * NT + tid;
           slot[u] = kNone;
           if (i >= r1) continue;
-          const uint32_t row = J.tmp_row[i];
+          const uint32_t row = rw[u];
           uint4 kw = make_uint4(0u, J.nk > 0 ? uint32_t(__ldg(J.kc[0] + row)) : 0u,
                                 J.nk > 1 ? uint32_t(__ldg(J.kc[1] + row)) : 0u,
                                 J.nk > 2 ? uint32_t(__ldg(J.kc[2] + row)) : 0u);
           bool cl = false;
           slot[u] = ht_insert_wide(J.ht, mask, kw, cl, &res->status);
+          if (cl) clm |= 1u << u;
         }
       }
 #pragma unroll
       for (int u = 0; u < E; ++u) {
         const uint32_t i = r + u * NT + tid;
         if (i >= r1) continue;
-        if (J.tmin && slot[u] != kNone) atomicMin(reinterpret_cast<int*>(&J.sbegin[slot[u]]), tv[u]);
         // The count before this row's increment is the row's rank among
         // the rows of its key: its place in the entry's range.
-        J.newslots[i] = slot[u] != kNone ? atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u) : 0u;
+        const uint32_t rank = slot[u] != kNone ? atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u) : 0u;
+        if (slot[u] != kNone) {
+          if (rank == 0)
+            *slot_row(J.ht, J.wide, slot[u]) = rw[u];
+          else if (J.tmin)
+            atomicMin(reinterpret_cast<int*>(&J.sbegin[slot[u]]), __ldg(J.tcol + rw[u]));
+        }
+        dup |= rank != 0;
+        J.newslots[i] = rank;
         J.tmp_slot[i] = slot[u];
       }
+      // The claimed slots are the level's entries: appended to the slot
+      // list, one counter advance per block sweep; an entry's id is its
+      // place in the list.
+      uint32_t ctot;
+      uint32_t pos = block_excl_scan<uint32_t>(__popc(clm), s_scan, &ctot);
+      if (tid == 0) s_base = ctot ? atomicAdd(&cs->n_new[set][j], ctot) : 0u;
+      __syncthreads();
+      pos += s_base;
+#pragma unroll
+      for (int u = 0; u < E; ++u)
+        if (clm >> u & 1u) J.slot_of[pos++] = slot[u];
     }
   }
+  if (__syncthreads_or(dup) && tid == 0) cs->dup[set] = 1u;
   if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
-
-  // D: the occupied slots of each table (a slot is occupied once a row has
-  // been counted in it) become the root's entries, in slot order, each with
-  // its range of offsets inside the root's range: per sweep of the block's
-  // part of a table, one advance of the entry counter and one of the
-  // root's fill cursor.
-  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_mask[j] + 2 : 0u; });
-  block_range(s_off[nj], lo, hi);
-  for (int j = 0; j < nj; ++j) {
-    const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
-    if (a0 >= a1) continue;
-    const RootJob& J = s_job[j];
-    const uint32_t r1 = a1 - s_off[j];
-    constexpr int ED = 2 * E;  // slots per thread per sweep
-    for (uint32_t r = a0 - s_off[j]; r < r1; r += ED * NT) {
-      uint32_t cnt[ED], occ = 0, n_occ = 0, sum = 0;
-      uint64_t kw[ED];
-      int32_t smin[ED];  // a tail level: the slot's MIN, read with the slot
-#pragma unroll
-      for (int u = 0; u < ED; ++u) {
-        const uint32_t sl_i = r + u * NT + tid;
-        cnt[u] = 0;
-        kw[u] = 0;
-        smin[u] = 0;
-        if (sl_i >= r1) continue;
-        if (J.tmin) smin[u] = int32_t(J.sbegin[sl_i]);
-        if (J.wide) {
-          cnt[u] = J.ht[2 * size_t(sl_i) + 1].y;
-          kw[u] = 0;  // wide entries keep only the parent (the root: 0)
-        } else {
-          const uint4 sl = J.ht[sl_i];
-          cnt[u] = sl.w;
-          kw[u] = sl_i == s_mask[j] + 1 ? kEmptyKey : ((uint64_t(sl.y) << 32) | sl.x);
-        }
-        if (cnt[u]) {
-          occ |= 1u << u;
-          ++n_occ;
-          sum += cnt[u];
-        }
-      }
-      unsigned long long tot;
-      const unsigned long long pre = block_excl_scan<unsigned long long>(
-          (static_cast<unsigned long long>(n_occ) << 32) | sum, s_scan64, &tot);
-      if (tid == 0) {
-        const uint32_t te = uint32_t(tot >> 32), tr = uint32_t(tot);
-        s_base = te ? atomicAdd(&cs->n_new[set][j], te) : 0u;
-        s_base2 = tr ? atomicAdd(J.pfill, tr) : 0u;
-      }
-      __syncthreads();
-      uint32_t e = J.base_e + s_base + uint32_t(pre >> 32);
-      uint32_t b = s_base2 + uint32_t(pre);  // the root's range starts at 0
-#pragma unroll
-      for (int u = 0; u < ED; ++u) {
-        if (!(occ >> u & 1u)) continue;
-        const uint32_t sl_i = r + u * NT + tid;
-        *slot_e(J.ht, J.wide, sl_i) = e;
-        if (J.tmin) J.tmin[e] = smin[u];
-        J.sbegin[sl_i] = b;
-        J.key[e] = kw[u];
-        J.count[e] = cnt[u];
-        J.begin[e] = b;
-        J.fill[e] = b;
-        if (J.cstate) J.cstate[e] = kUnforced;
-        if (J.cnkeys) J.cnkeys[e] = 0;
-        if (J.cfirst) J.cfirst[e] = 0;
-        ++e;
-        b += cnt[u];
-      }
-      __syncthreads();
-    }
-  }
-  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
-  if (tid < uint32_t(nj)) s_nn[tid] = cs->n_new[set][tid];
+  // Every key has exactly one row: D places the rows and there is no E.
+  const bool scatter = ld_acquire_gpu(&cs->dup[set]) != 0;
+  if (tid < uint32_t(nj)) s_nn[tid] = ld_acquire_gpu(&cs->n_new[set][tid]);
   __syncthreads();
 
-  // The level's bookkeeping (block 0, while the others scatter; nothing in
-  // the scatter reads it).  The entries' fill cursors stay where the
-  // scatter leaves them: forcing the next level resets the cursors of the
-  // parents it regroups.
+  // The level's bookkeeping (block 0, while the others assign entries;
+  // nothing in D or E reads it).  The table's dirty slots are the listed
+  // ones from here on.  The entries' fill cursors stay where D leaves them:
+  // forcing the next level resets the cursors of the parents it regroups.
   if (blockIdx.x == 0 && tid < uint32_t(nj)) {
     const int j = tid;
     const RootJob& J = s_job[j];
@@ -1248,6 +1292,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
         P.begin[0] = 0;
         P.count[0] = np;
       }
+      if (!scatter) *J.pfill = np;  // D places the rows without the cursor
       atomicAdd(&res->ctr[FJ_CTR_ROOTS_BUILT], 1ull);
       atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
                1ull << fj.jobs[j].x);
@@ -1260,8 +1305,90 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       L.cleared = 1;
       L.n_req = 0;
       L.n_in = 0;
+      L.n_listed = nn;
+      L.last_slots = s_mask[j] + 2;
+      L.ht_state = kHtListed;
     }
   }
+
+  // D: the listed slots become the root's entries (entry i of the level is
+  // list position i), each with its range of offsets inside the root's
+  // range, ED consecutive entries per thread.  When every key has one row
+  // (no scatter) entry i's range is offset i and the entry places its row
+  // (the row that claimed the slot); otherwise the ranges follow a block
+  // scan of the counts, one advance of the root's fill cursor per sweep.
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_nn[j] : 0u; });
+  block_range(s_off[nj], lo, hi);
+  for (int j = 0; j < nj; ++j) {
+    const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
+    if (a0 >= a1) continue;
+    const RootJob& J = s_job[j];
+    const uint32_t r1 = a1 - s_off[j];
+    constexpr int ED = E;  // entries per thread per sweep
+    for (uint32_t r = a0 - s_off[j]; r < r1; r += ED * NT) {
+      uint32_t sl[ED], cnt[ED], crow[ED], sum = 0;
+      uint64_t kw[ED];
+      int32_t smin[ED];  // a tail level: the MIN of the rows after the first
+      const uint32_t i0 = r + tid * ED;
+#pragma unroll
+      for (int u = 0; u < ED; ++u) sl[u] = i0 + u < r1 ? J.slot_of[i0 + u] : kNone;
+#pragma unroll
+      for (int u = 0; u < ED; ++u) {
+        cnt[u] = 0;
+        crow[u] = 0;
+        kw[u] = 0;
+        smin[u] = 0;
+        if (sl[u] == kNone) continue;
+        if (J.tmin) smin[u] = int32_t(J.sbegin[sl[u]]);
+        if (J.wide) {
+          const uint4 v = J.ht[2 * size_t(sl[u]) + 1];
+          cnt[u] = v.y;
+          crow[u] = v.z;
+          kw[u] = 0;  // wide entries keep only the parent (the root: 0)
+        } else {
+          const uint4 v = J.ht[sl[u]];
+          cnt[u] = v.w;
+          crow[u] = v.z;
+          kw[u] = sl[u] == s_mask[j] + 1 ? kEmptyKey : ((uint64_t(v.y) << 32) | v.x);
+        }
+        sum += cnt[u];
+      }
+      if (J.tmin) {  // and the first row's value
+#pragma unroll
+        for (int u = 0; u < ED; ++u)
+          if (sl[u] != kNone) smin[u] = min(smin[u], __ldg(J.tcol + crow[u]));
+      }
+      uint32_t b = i0;  // the root's range starts at 0
+      if (scatter) {
+        uint32_t tot;
+        const uint32_t pre = block_excl_scan<uint32_t>(sum, s_scan, &tot);
+        if (tid == 0) s_base2 = tot ? atomicAdd(J.pfill, tot) : 0u;
+        __syncthreads();
+        b = s_base2 + pre;
+      }
+#pragma unroll
+      for (int u = 0; u < ED; ++u) {
+        if (sl[u] == kNone) continue;
+        const uint32_t e = J.base_e + i0 + u;
+        *slot_e(J.ht, J.wide, sl[u]) = e;
+        if (J.tmin) J.tmin[e] = smin[u];
+        if (cnt[u] == 1) J.perm[b] = crow[u];
+        J.sbegin[sl[u]] = b;
+        J.key[e] = kw[u];
+        J.count[e] = cnt[u];
+        J.begin[e] = b;
+        J.fill[e] = b;
+        if (J.cstate) J.cstate[e] = kUnforced;
+        if (J.cnkeys) J.cnkeys[e] = 0;
+        if (J.cfirst) J.cfirst[e] = 0;
+        b += cnt[u];
+      }
+      if (scatter) __syncthreads();
+    }
+  }
+
+  if (!scatter) return;
+  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
 
   // E: every passing row to its place in its entry's range (the entry's
   // first offset, kept per slot by D, plus the row's rank from C).

@@ -257,6 +257,40 @@ def chooser_query(q, min_rows=10_000, max_rows=50_000, base_seed=5, kind=None):
     return atoms, kind
 
 
+def chooser_pool(n_rel, min_rows=1_000_000, max_rows=16_000_000, seed=17):
+    """n_rel two-column relations to compose chooser training queries from
+    (pool_query): row count log-uniform in [min_rows, max_rows], each with
+    its own Zipf exponent s uniform in [0.8, 1.6], both columns Zipf(s) over
+    a key domain of the relation's row count through a seeded permutation
+    (the columns of chooser_query)."""
+    rng = _rng(seed)
+    pool = []
+    for i in range(n_rel):
+        n = int(round(np.exp(rng.uniform(np.log(min_rows), np.log(max_rows)))))
+        s = float(rng.uniform(0.8, 1.6))
+        pool.append({"name": f"P{i}", "cols": [_zipf_col(n, n, s, rng) for _ in range(2)]})
+    return pool
+
+
+def pool_query(pool, q, base_seed=11):
+    """Query q (seed base_seed + q) over the relations of a pool, with the
+    shapes of chooser_query: a snowflake (q even) or a 5-cycle (q odd), each
+    atom a different pool relation drawn at random, its two columns bound in
+    random order.  Returns (atoms, kind)."""
+    rng = _rng(base_seed + q)
+    kind = "snowflake" if q % 2 == 0 else "cycle"
+    if kind == "snowflake":
+        shape = [[0, 1], [0, 2], [1, 3], [2, 4], [3, 5]]
+    else:
+        shape = [[0, 1], [1, 2], [2, 3], [3, 4], [4, 0]]
+    idx = rng.choice(len(pool), len(shape), replace=False)
+    atoms = []
+    for i, vs in zip(idx, shape):
+        cols = [0, 1] if rng.random() < 0.5 else [1, 0]
+        atoms.append(atom(pool[int(i)], vs, rel_cols=cols))
+    return atoms, kind
+
+
 # ---------------------------------------------------------------------------
 # Small random queries for property tests
 # ---------------------------------------------------------------------------

@@ -350,3 +350,60 @@ def test_materialized_output_above_the_first_buffer_is_retried(fj, ctx):
     t = got.tuples.cpu().numpy()
     assert len(t) == got.count
     assert len({(a, b) for _, a, b in t.tolist()}) == 1100 * 1000
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_root_tables_reused_across_executions(fj, ctx, seed):
+    """A root build clears only the slots the previous build of the same
+    table listed (the first build, and any after a build by the multi-launch
+    path, clear the whole table).  One prepared query, executed again and
+    again -- in between, once inside a batch of concurrent branches, whose
+    root levels the multi-launch path builds -- gives the oracle's COUNT and
+    MINs every time: unique keys (each row placed by its entry) and repeated
+    ones (placed by the scatter), one- to three-column keys, small and large
+    key domains."""
+    rng = np.random.default_rng(seed)
+    domain, rows = [(3, 40), (40, 600), (5000, 3000)][seed % 3]
+    atoms = G.random_query(900 + seed, max_atoms=4, max_rows=rows, domain=domain, max_vars=5,
+                           max_arity=3)
+    mins = oracle.query_vars(atoms)[:2]
+    want_c, want_m, _ = oracle.binary_join(atoms, min_vars=mins)
+    dev, _ = device_atoms(fj, ctx, atoms)
+    order = [int(a) for a in rng.permutation(len(atoms))]
+    plan = fj.binary_to_free_plan(dev, order, factor=True)
+    p = fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=mins)
+    for k in range(5):
+        if k == 2:
+            b = fj.Batch(ctx, [p], graph=True, concurrent=True)
+            (r,) = b.execute()
+            b.free()
+        else:
+            p.reset()
+            r = p.execute()
+        assert (r.count, r.mins) == (want_c, want_m), k
+    p.free()
+
+
+def test_root_tables_reused_star_join(fj, ctx):
+    """The star join's dimension roots (unique keys: no scatter pass) and a
+    variant whose dimensions repeat keys (scatter pass), each executed three
+    times on one prepared query with the per-entry tail MINs, equal the
+    direct-address join every time."""
+    fact, dims = G.star_schema(n_fact=200_000, dims=(1000, 2500, 5000, 10_000), s=1.1, seed=7)
+    want = closed.star_join_direct(fact["cols"], [tuple(d["cols"]) for d in dims],
+                                   [G.STAR_THETA] * 4)
+    for repeat in (False, True):
+        if repeat:
+            # Every dimension row twice: each key has two rows.
+            dims = [dict(d, cols=[np.concatenate([c, c]) for c in d["cols"]]) for d in dims]
+            want = closed.star_join_direct(fact["cols"], [tuple(d["cols"]) for d in dims],
+                                           [G.STAR_THETA] * 4)
+        atoms = G.star_query(fact, dims, theta=G.STAR_THETA)
+        dev, _ = device_atoms(fj, ctx, atoms)
+        plan = fj.binary_to_free_plan(dev, list(range(5)), factor=True)
+        p = fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=[4, 5, 6, 7])
+        for _ in range(3):
+            p.reset()
+            r = p.execute()
+            assert (r.count, r.mins) == want, repeat
+        p.free()
