@@ -249,7 +249,7 @@ void force(fj_prepared* P, const int2* d_jobs, int n_jobs, uint32_t ub_rows, uin
     uint32_t spin = uint32_t(std::min<uint64_t>(P->opts.spin_limit, 0xffffffffull));
     void* args[] = {&fj, &cs, &set, &all, &test_timeout, &rd, &spin};
     CK(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_force_roots),
-                                   dim3(P->roots_grid), dim3(kRootThreads), args, 0, s));
+                                   dim3(P->roots_grid), dim3(kRootThreads), args, kRootSmem, s));
     if (test_timeout) {
       // The test of the bounded waits stops the execution here: nothing may
       // run on the levels the build left unbuilt.
@@ -574,7 +574,6 @@ static void compile(fj_prepared* P) {
       }
       L.ht_state = kHtUnknown;  // fresh memory: the first build clears it all
       L.n_listed = 0;
-      L.used_hi = L.ht_cap_max + 1;
       if (!L.wide) {
         // Bloom filter: about 8 bits per row, 256 B to 32 KB.
         uint32_t words = 64;
@@ -975,8 +974,10 @@ static void setup_roots(fj_prepared* P) {
   int coop = 0;
   CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, P->ctx->device));
   if (!coop) return;
+  CK(cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_force_roots),
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(kRootSmem)));
   int b = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force_roots, kRootThreads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force_roots, kRootThreads, kRootSmem));
   if (b < 1) return;
   P->roots_state = P->alloc<RootsState>(1);
   P->roots_grid = P->ctx->n_sm * std::min(b, 2);

@@ -101,12 +101,10 @@ struct LevelDev {
   uint32_t n_tmp;      // (row, slot) pairs staged by the current force
   // State of the table between executions (kept across resets):
   // kHtListed: empty except the slots slot_of[0, n_listed) (and, for a
-  // tail level, sbegin is INT32_MAX except there); kHtUnknown: any slot
-  // below used_hi may be dirty.
+  // tail level, sbegin is INT32_MAX except there); kHtUnknown: any slot may
+  // be dirty.
   uint32_t ht_state = kHtUnknown;
   uint32_t n_listed = 0;
-  uint32_t used_hi = 0;  // slots [0, used_hi) may have been written
-  uint32_t last_slots = 0;  // slots the last root build's table spanned
 };
 
 struct AtomDev {

@@ -419,7 +419,6 @@ __global__ void k_force_prepare(ForceJobs fj) {
   L.mask = cap - 1;
   // This build leaves no list of the slots it writes.
   L.ht_state = kHtUnknown;
-  L.used_hi = max(L.used_hi, cap + 1);
   // Keep the filter only with at least 4 bits per key.
   L.filter_on = L.filter && uint64_t(L.n_in) * 4 <= uint64_t(L.filter_words) * 32;
 }
@@ -732,20 +731,27 @@ __global__ void k_force_reset_req(ForceJobs fj) {
 // first schema level) reads the whole base table; for a node whose jobs are
 // all roots, the passes of a force run in one kernel whose blocks are all
 // resident (cudaLaunchCooperativeKernel), separated by grid barriers:
-//   A  compact the rows that pass the selection,
-//   B  size and clear each table and filter,
-//   C  insert the keys and count rows per key,
-//   D  make each occupied slot an entry with its range of offsets,
-//   E  scatter the offsets,
-//   F  reset the fill cursors and record the level as forced.
-// Each pass splits the work of all jobs into one contiguous range per block
-// and takes several independent elements per thread at a time (the passes
-// are chains of dependent L2 accesses); offsets come from counters per job,
-// advanced once per sweep of 8192 rows in A and of 2048 slots in D.  Every barrier wait is bounded: on expiry the kernel sets
-// kStTimeout and its blocks return; the host reports FJ_ERR_TIMEOUT.
+//   A  clear each Bloom filter, and each table's slots the previous build
+//      listed (a table is cleared whole only when no build left a list),
+//   C  select the rows, insert their keys, count rows per key, list the
+//      slots, stage (row, slot, rank) per passing row,
+//   D  make each listed slot an entry with its range of offsets; place the
+//      row of every key that has one; record the level as forced,
+//   E  (only when some key repeats) scatter the staged rows.
+// A table spans its whole allocation, so C need not wait for the count of
+// passing rows to size it.  Each pass splits the work of all jobs into one
+// contiguous range per block and takes several independent elements per
+// thread at a time (the passes are chains of dependent L2 accesses);
+// offsets come from counters per job, advanced once per block sweep.
+// Every barrier wait is bounded: on expiry the kernel sets kStTimeout and
+// its blocks return; the host reports FJ_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
 
 constexpr int kRootThreads = 512;
+constexpr int kRootRows = 12;  // rows per thread per sweep of C
+// Dynamic shared memory of k_force_roots: per warp a queue of 32 x kRootRows
+// (row, key or slot, rank) triples.
+constexpr size_t kRootSmem = size_t(kRootThreads) * kRootRows * 3 * sizeof(uint32_t);
 
 struct RootsState {        // zero at the start of each execution (k_reset)
   unsigned int bar_count;  // block arrivals at grid barriers this execution
@@ -759,12 +765,6 @@ struct RootsState {        // zero at the start of each execution (k_reset)
 };
 
 constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about a second)
-
-// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
-constexpr uint32_t kPrefetchChunk = 16384;
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   unsigned int v;
@@ -857,8 +857,6 @@ struct RootJob {
   uint32_t* slot_of;   // per entry: its slot (the list the next build clears)
   uint32_t state;      // the table's state when the launch began (LevelDev::ht_state)
   uint32_t n_listed;   // ... and its listed slots
-  uint32_t used_hi;
-  uint32_t last_slots;
   int32_t* tmin;       // per entry: MIN of tcol over its rows (or null)
   const int32_t* tcol;
   uint32_t* perm;
@@ -870,7 +868,6 @@ struct RootJob {
   uint32_t* cfirst;
   uint32_t* cnkeys;
   uint32_t* pfill;  // the root's fill cursor
-  float load;
   int n_preds;
   const int32_t* pcol[FJ_MAX_PREDS];
   int pop[FJ_MAX_PREDS];
@@ -941,17 +938,23 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
                                                                  int set, int request_all,
                                                                  int test_timeout,
                                                                  ResultDev* res, uint32_t spin) {
-  constexpr int E = 4;  // independent elements per thread in C, D and E
-  constexpr uint32_t NT = kRootThreads;
+  constexpr int E = 4;  // independent elements per thread in C's inserts, D and E
+  constexpr uint32_t NT = kRootThreads, NW = NT / 32, QW = 32 * kRootRows;
   const int nj = fj.n_jobs;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  // Per warp, C's queue of the rows of a sweep that pass the selection:
+  // QW rows, QW keys (then their slots), QW ranks.
+  extern __shared__ __align__(16) uint32_t s_queue[];
+  uint32_t* q_row = s_queue + size_t(warp) * 3 * QW;
+  uint32_t* q_key = q_row + QW;
+  uint32_t* q_rank = q_key + QW;
   __shared__ RootJob s_job[FJ_MAX_ATOMS];
   __shared__ uint32_t s_off[FJ_MAX_ATOMS + 1];
-  __shared__ uint32_t s_mask[FJ_MAX_ATOMS], s_fon[FJ_MAX_ATOMS];
-  __shared__ uint32_t s_np[FJ_MAX_ATOMS], s_nn[FJ_MAX_ATOMS];  // rows passing, new keys
+  __shared__ uint32_t s_mask[FJ_MAX_ATOMS];
+  __shared__ uint32_t s_np[FJ_MAX_ATOMS], s_nn[FJ_MAX_ATOMS];  // rows passing, keys
+  __shared__ uint32_t s_wq[NW], s_wc[NW];  // per warp: queued rows, new keys
   __shared__ uint32_t s_scan[33];
-  __shared__ unsigned long long s_scan64[33];
-  __shared__ uint32_t s_base, s_base2;
+  __shared__ uint32_t s_base2;
   // Grid barriers completed before this launch (an execution may launch the
   // build more than once); only thread 0 takes part in the barriers.
   uint32_t bar_target = tid == 0 ? ld_acquire_gpu(&cs->bar_gen) : 0u;
@@ -979,10 +982,8 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     J.newslots = a.newslots;
     J.sbegin = L.sbegin;
     J.slot_of = L.slot_of;
-    J.state = L.slot_of ? L.ht_state : kHtUnknown;
+    J.state = L.ht_state;
     J.n_listed = L.n_listed;
-    J.used_hi = L.used_hi;
-    J.last_slots = L.last_slots;
     J.tmin = L.tmin;
     J.tcol = L.tmin ? a.cols[L.tmin_col] : nullptr;
     J.perm = a.perm;
@@ -994,66 +995,29 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     J.cfirst = L.child_first;
     J.cnkeys = L.child_nkeys;
     J.pfill = P.fill;
-    J.load = a.load > 0.f ? a.load : 0.5f;
     J.n_preds = a.n_preds;
     for (int p = 0; p < a.n_preds; ++p) {
       J.pcol[p] = a.cols[a.pred_col[p]];
       J.pop[p] = a.pred_op[p];
       J.pval[p] = a.pred_val[p];
     }
+    // The table spans its whole allocation (sized for every row of the
+    // atom at its load factor): it is never cleared as a whole once built,
+    // so a larger span costs nothing, and its size need not wait for the
+    // count of passing rows.
+    s_mask[tid] = L.ht_cap_max - 1;
   }
   if (blockIdx.x == 0 && tid < uint32_t(FJ_MAX_ATOMS)) {
     cs->n_pass[set ^ 1][tid] = 0;
     cs->n_new[set ^ 1][tid] = 0;
     if (tid == 0) cs->dup[set ^ 1] = 0;
   }
+  __syncthreads();
   uint32_t lo, hi;
 
-  // A: rows that pass the selection, compacted into tmp_row, 16 rows per
-  // thread per sweep of the block's part of a job (one counter advance per
-  // sweep).  One-column narrow keys travel with the row (in tmp_slot until
-  // C replaces them by the slot), read while the rows are at hand.
-  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_job[j].src : 0u; });
-  block_range(s_off[nj], lo, hi);
-  for (int j = 0; j < nj; ++j) {
-    const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
-    if (a0 >= a1) continue;
-    const RootJob& J = s_job[j];
-    const bool k1 = !J.wide && J.nk == 1;
-    const uint32_t r1 = a1 - s_off[j];
-    for (uint32_t r = a0 - s_off[j]; r < r1; r += 16 * NT) {
-      uint32_t row[16];
-      int32_t key[16];
-      // Base-table rows: every key load goes out with the selection loads
-      // (one round trip to memory instead of two).
-      const bool early = k1 && J.ident;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const uint32_t i = r + k * NT + tid;
-        key[k] = (early && i < r1) ? __ldg(J.kc[0] + i) : 0;
-      }
-      const uint32_t pass = root_rows_pass<16>(J, r, r1, row);
-      if (k1 && !early) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) key[k] = (pass >> k & 1u) ? __ldg(J.kc[0] + row[k]) : 0;
-      }
-      uint32_t tot;
-      uint32_t o = block_excl_scan<uint32_t>(__popc(pass), s_scan, &tot);
-      if (tid == 0) s_base = tot ? atomicAdd(&cs->n_pass[set][j], tot) : 0u;
-      __syncthreads();
-      o += s_base;
-#pragma unroll
-      for (int k = 0; k < 16; ++k)
-        if (pass >> k & 1u) {
-          J.tmp_row[o] = row[k];
-          if (k1) J.tmp_slot[o] = uint32_t(key[k]);
-          ++o;
-        }
-      __syncthreads();
-    }
-  }
-  // Every active job's Bloom filter to zero (its size does not depend on
-  // the passing rows; B decides whether it is used).
+  // A: every active job's Bloom filter to zero; its table back to empty --
+  // the slots its previous build listed (and a tail level's running MINs
+  // there back to INT32_MAX), or, when no build left a list, every slot.
   jobs_prefix(nj, s_off, [&](int j) {
     return s_job[j].act && s_job[j].filter ? s_job[j].filter_words / 4 : 0u;
   });
@@ -1061,215 +1025,221 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     const int j = job_at(s_off, nj, x);
     reinterpret_cast<uint4*>(s_job[j].filter)[x - s_off[j]] = make_uint4(0u, 0u, 0u, 0u);
   }
-  // The slots the previous build of a table listed back to empty (and a
-  // tail level's running MINs back to INT32_MAX): the rest of the table is
-  // empty already.  The table's span at the previous build (the same query
-  // spans the same slots again) is prefetched into L2 by bulk copies, so
-  // that the inserts and D meet it there.
   jobs_prefix(nj, s_off, [&](int j) {
     const RootJob& J = s_job[j];
-    if (!J.act || J.state != kHtListed) return 0u;
-    const uint32_t tb = J.last_slots * (J.wide ? 32u : 16u);
-    const uint32_t mb = J.tmin ? (J.last_slots * 4u) & ~15u : 0u;  // whole 16-byte units
-    return (tb + kPrefetchChunk - 1) / kPrefetchChunk + (mb + kPrefetchChunk - 1) / kPrefetchChunk;
-  });
-  // Chunk x goes to block x mod grid: the bulk copies of one block are
-  // served one after another.
-  for (uint32_t x = blockIdx.x + gridDim.x * tid; x < s_off[nj]; x += gridDim.x * NT) {
-    const int j = job_at(s_off, nj, x);
-    const RootJob& J = s_job[j];
-    const uint32_t tb = J.last_slots * (J.wide ? 32u : 16u);  // table bytes
-    const uint32_t nt = (tb + kPrefetchChunk - 1) / kPrefetchChunk;
-    const uint32_t c = x - s_off[j];
-    if (c < nt) {
-      const uint32_t off = c * kPrefetchChunk;
-      prefetch_l2(reinterpret_cast<const char*>(J.ht) + off, min(kPrefetchChunk, tb - off));
-    } else {  // then the running MINs
-      const uint32_t off = (c - nt) * kPrefetchChunk;
-      const uint32_t mb = (J.last_slots * 4u) & ~15u;
-      prefetch_l2(reinterpret_cast<const char*>(J.sbegin) + off, min(kPrefetchChunk, mb - off));
-    }
-  }
-  jobs_prefix(nj, s_off, [&](int j) {
-    const RootJob& J = s_job[j];
-    return J.act && J.state == kHtListed ? J.n_listed : 0u;
+    if (!J.act) return 0u;
+    return J.state == kHtListed ? J.n_listed : J.ht_cap_max + 1;
   });
   for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
     const int j = job_at(s_off, nj, x);
     const RootJob& J = s_job[j];
-    const uint32_t sl = J.slot_of[x - s_off[j]];
+    const uint32_t sl = J.state == kHtListed ? J.slot_of[x - s_off[j]] : x - s_off[j];
     slot_clear(J.ht, J.wide, sl);
     if (J.tmin) J.sbegin[sl] = uint32_t(INT32_MAX);
   }
   if (!grid_sync(cs, &res->status, spin, ++bar_target, test_timeout != 0)) return;
-  if (tid < uint32_t(nj)) s_np[tid] = cs->n_pass[set][tid];
-  __syncthreads();
-
-  // Size each table for its passing rows.  From here on a failed launch
-  // leaves the table in an unknown state; a complete one lists its slots.
-  bool full_clear = false;  // some table is in an unknown state: B clears it
-  for (int j = 0; j < nj; ++j) full_clear |= s_job[j].act && s_job[j].state != kHtListed;
-  if (tid < uint32_t(nj)) {
-    const RootJob& J = s_job[tid];
-    const uint32_t n_in = s_np[tid];
-    const float want = float(n_in) / J.load;
-    uint32_t cap = 16;
-    while (float(cap) < want && cap < J.ht_cap_max) cap <<= 1;
-    s_mask[tid] = cap - 1;
-    s_fon[tid] = J.filter && uint64_t(n_in) * 4 <= uint64_t(J.filter_words) * 32;
-    if (blockIdx.x == 0 && J.act) {
-      LevelDev& L = fj.atoms[fj.jobs[tid].x].L[fj.jobs[tid].y];
-      L.mask = cap - 1;
-      L.filter_on = s_fon[tid];
-      L.n_in = n_in;
-      L.ht_state = kHtUnknown;
-      L.used_hi = max(J.used_hi, cap + 1);
-    }
-  }
-  __syncthreads();
-
-  // B (only after a build that left no list, or the first): clear every
-  // slot of such a table that may have been written.
-  if (full_clear) {
-    jobs_prefix(nj, s_off, [&](int j) {
-      const RootJob& J = s_job[j];
-      if (!J.act || J.state == kHtListed) return 0u;
-      return max(J.used_hi, s_mask[j] + 2) * (J.wide ? 2u : 1u);
-    });
-    for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
-      const int j = job_at(s_off, nj, x);
-      const RootJob& J = s_job[j];
-      const uint32_t u = x - s_off[j];
-      if (J.wide)
-        J.ht[u] = (u & 1u) ? make_uint4(kNone, 0u, 0u, 0u) : make_uint4(kNone, kNone, kNone, kNone);
-      else
-        J.ht[u] = make_uint4(0xffffffffu, 0xffffffffu, kNone, 0u);
-      // A tail level: sbegin holds each slot's running MIN of the tail
-      // column until D (one word per slot: every second uint4 of a wide
-      // table).
-      if (J.tmin && (!J.wide || !(u & 1u))) J.sbegin[J.wide ? u / 2 : u] = uint32_t(INT32_MAX);
-    }
-    if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
+  // From here on a failed launch leaves the tables in an unknown state; a
+  // complete one lists the slots it used.
+  if (blockIdx.x == 0 && tid < uint32_t(nj) && s_job[tid].act) {
+    LevelDev& L = fj.atoms[fj.jobs[tid].x].L[fj.jobs[tid].y];
+    L.mask = s_mask[tid];
+    L.ht_state = kHtUnknown;
   }
 
-  // C: insert every passing row's key (E per thread, their first
-  // compare-and-swaps in flight together) and count rows per key.  The
-  // key's first row (rank 0) leaves itself in the slot: D places it when it
-  // is the key's only row, and a tail level's MIN starts from its value
-  // (the other rows fold theirs into the slot's running MIN).
-  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_np[j] : 0u; });
+  // C: per sweep, kRootRows rows per thread: the selection and key loads of
+  // all of them in flight together, the passing rows into the warp's queue,
+  // then the queue's keys inserted E per lane with their first
+  // compare-and-swaps in flight together, each row counted in its key's
+  // slot.  The count before a row's increment is its rank among the rows
+  // of its key (its place in the entry's range); the rank-0 row leaves
+  // itself in the slot (D places it when it is the key's only row, and a
+  // tail level's MIN starts from its value; the other rows fold theirs into
+  // the slot's running MIN) and puts the slot on the table's list, whose
+  // order numbers the entries.  Per sweep one advance of the job's row and
+  // key counters: the queues go to the staging arrays (for E) and the list
+  // at those offsets.
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_job[j].src : 0u; });
   block_range(s_off[nj], lo, hi);
   bool dup = false;  // some key of this block's rows has another row before it
   for (int j = 0; j < nj; ++j) {
     const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
     if (a0 >= a1) continue;
     const RootJob& J = s_job[j];
+    const bool k1 = !J.wide && J.nk == 1;
     const uint32_t mask = s_mask[j];
-    for (uint32_t r = a0 - s_off[j]; r < a1 - s_off[j]; r += E * NT) {
-      const uint32_t r1 = a1 - s_off[j];
-      uint32_t slot[E], rw[E], clm = 0;  // clm: bit u, row u claimed its slot
+    const uint32_t r1 = a1 - s_off[j];
+    for (uint32_t r = a0 - s_off[j]; r < r1; r += kRootRows * NT) {
+      uint32_t qn;
+      {
+        uint32_t row[kRootRows];
+        int32_t key[kRootRows];
+        // Base-table rows: every key load goes out with the selection loads
+        // (one round trip to memory instead of two).
+        const bool early = k1 && J.ident;
 #pragma unroll
-      for (int u = 0; u < E; ++u) {
-        const uint32_t i = r + u * NT + tid;
-        rw[u] = i < r1 ? J.tmp_row[i] : 0u;
-      }
-      if (!J.wide) {
-        uint64_t kw[E];
-        uint32_t h[E];
-        unsigned long long old[E];
+        for (int k = 0; k < kRootRows; ++k) {
+          const uint32_t i = r + k * NT + tid;
+          key[k] = (early && i < r1) ? __ldg(J.kc[0] + i) : 0;
+        }
+        const uint32_t pass = root_rows_pass<kRootRows>(J, r, r1, row);
+        if (k1 && !early) {
 #pragma unroll
-        for (int u = 0; u < E; ++u) {
-          const uint32_t i = r + u * NT + tid;
-          kw[u] = 0;
-          if (i >= r1) continue;
-          if (J.nk == 1) {
-            kw[u] = J.tmp_slot[i];
-          } else {
-            const uint32_t row = rw[u];
-            kw[u] = pack_key(0u, J.nk, J.nk > 0 ? __ldg(J.kc[0] + row) : 0,
-                             J.nk > 1 ? __ldg(J.kc[1] + row) : 0);
+          for (int k = 0; k < kRootRows; ++k)
+            key[k] = (pass >> k & 1u) ? __ldg(J.kc[0] + row[k]) : 0;
+        }
+        const uint32_t np = __popc(pass);
+        const uint32_t incl = warp_incl_scan(np);
+        qn = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t qp = incl - np;
+#pragma unroll
+        for (int k = 0; k < kRootRows; ++k)
+          if (pass >> k & 1u) {
+            q_row[qp] = row[k];
+            q_key[qp] = uint32_t(key[k]);
+            ++qp;
           }
-        }
+      }
+      __syncwarp();
+      uint32_t n_first = 0;  // this lane's rank-0 rows
+      for (uint32_t i0 = 0; i0 < qn; i0 += E * 32) {
+        uint32_t slot[E], rw[E];
 #pragma unroll
         for (int u = 0; u < E; ++u) {
-          const uint32_t i = r + u * NT + tid;
-          if (i >= r1 || kw[u] == kEmptyKey) continue;
-          h[u] = hash_key(kw[u]) & mask;
-          old[u] = atomicCAS(slot_key(J.ht, h[u]), kEmptyKey, kw[u]);
+          const uint32_t i = i0 + u * 32 + lane;
+          rw[u] = i < qn ? q_row[i] : 0u;
         }
+        if (!J.wide) {
+          uint64_t kw[E];
+          uint32_t h[E];
+          unsigned long long old[E];
 #pragma unroll
-        for (int u = 0; u < E; ++u) {
-          const uint32_t i = r + u * NT + tid;
-          slot[u] = kNone;
-          if (i >= r1) continue;
-          bool cl = false;
-          if (kw[u] == kEmptyKey)
-            slot[u] = ht_insert(J.ht, mask, kw[u], cl, &res->status);
-          else
-            slot[u] = ht_insert_from(J.ht, mask, kw[u], h[u], old[u], cl, &res->status);
-          if (cl) {
-            clm |= 1u << u;
-            if (s_fon[j]) {
+          for (int u = 0; u < E; ++u) {
+            const uint32_t i = i0 + u * 32 + lane;
+            kw[u] = 0;
+            if (i >= qn) continue;
+            if (k1) {
+              kw[u] = q_key[i];
+            } else {
+              const uint32_t row = rw[u];
+              kw[u] = pack_key(0u, J.nk, J.nk > 0 ? __ldg(J.kc[0] + row) : 0,
+                               J.nk > 1 ? __ldg(J.kc[1] + row) : 0);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < E; ++u) {
+            const uint32_t i = i0 + u * 32 + lane;
+            if (i >= qn || kw[u] == kEmptyKey) continue;
+            h[u] = hash_key(kw[u]) & mask;
+            old[u] = atomicCAS(slot_key(J.ht, h[u]), kEmptyKey, kw[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < E; ++u) {
+            const uint32_t i = i0 + u * 32 + lane;
+            slot[u] = kNone;
+            if (i >= qn) continue;
+            bool cl = false;
+            if (kw[u] == kEmptyKey)
+              slot[u] = ht_insert(J.ht, mask, kw[u], cl, &res->status);
+            else
+              slot[u] = ht_insert_from(J.ht, mask, kw[u], h[u], old[u], cl, &res->status);
+            if (cl && J.filter) {
               const uint32_t fh = filter_hash(kw[u]);
               atomicOr(&J.filter[fh & (J.filter_words - 1)], bloom_bits(fh));
             }
           }
+        } else {
+#pragma unroll
+          for (int u = 0; u < E; ++u) {
+            const uint32_t i = i0 + u * 32 + lane;
+            slot[u] = kNone;
+            if (i >= qn) continue;
+            const uint32_t row = rw[u];
+            uint4 kw = make_uint4(0u, J.nk > 0 ? uint32_t(__ldg(J.kc[0] + row)) : 0u,
+                                  J.nk > 1 ? uint32_t(__ldg(J.kc[1] + row)) : 0u,
+                                  J.nk > 2 ? uint32_t(__ldg(J.kc[2] + row)) : 0u);
+            bool cl = false;
+            slot[u] = ht_insert_wide(J.ht, mask, kw, cl, &res->status);
+          }
         }
-      } else {
 #pragma unroll
         for (int u = 0; u < E; ++u) {
-          const uint32_t i = r + u * NT + tid;
-          slot[u] = kNone;
-          if (i >= r1) continue;
-          const uint32_t row = rw[u];
-          uint4 kw = make_uint4(0u, J.nk > 0 ? uint32_t(__ldg(J.kc[0] + row)) : 0u,
-                                J.nk > 1 ? uint32_t(__ldg(J.kc[1] + row)) : 0u,
-                                J.nk > 2 ? uint32_t(__ldg(J.kc[2] + row)) : 0u);
-          bool cl = false;
-          slot[u] = ht_insert_wide(J.ht, mask, kw, cl, &res->status);
-          if (cl) clm |= 1u << u;
+          const uint32_t i = i0 + u * 32 + lane;
+          if (i >= qn) continue;
+          uint32_t rank = 0;
+          if (slot[u] != kNone) {
+            rank = atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u);
+            if (rank == 0) {
+              *slot_row(J.ht, J.wide, slot[u]) = rw[u];
+              ++n_first;
+            } else {
+              dup = true;
+              if (J.tmin)
+                atomicMin(reinterpret_cast<int*>(&J.sbegin[slot[u]]), __ldg(J.tcol + rw[u]));
+            }
+          }
+          q_key[i] = slot[u];
+          q_rank[i] = rank;
         }
       }
-#pragma unroll
-      for (int u = 0; u < E; ++u) {
-        const uint32_t i = r + u * NT + tid;
-        if (i >= r1) continue;
-        // The count before this row's increment is the row's rank among
-        // the rows of its key: its place in the entry's range.
-        const uint32_t rank = slot[u] != kNone ? atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u) : 0u;
-        if (slot[u] != kNone) {
-          if (rank == 0)
-            *slot_row(J.ht, J.wide, slot[u]) = rw[u];
-          else if (J.tmin)
-            atomicMin(reinterpret_cast<int*>(&J.sbegin[slot[u]]), __ldg(J.tcol + rw[u]));
-        }
-        dup |= rank != 0;
-        J.newslots[i] = rank;
-        J.tmp_slot[i] = slot[u];
+      // Offsets of this sweep's rows and keys: one advance of each counter
+      // per block.
+      n_first = __reduce_add_sync(0xffffffffu, n_first);
+      if (lane == 0) {
+        s_wq[warp] = qn;
+        s_wc[warp] = n_first;
       }
-      // The claimed slots are the level's entries: appended to the slot
-      // list, one counter advance per block sweep; an entry's id is its
-      // place in the list.
-      uint32_t ctot;
-      uint32_t pos = block_excl_scan<uint32_t>(__popc(clm), s_scan, &ctot);
-      if (tid == 0) s_base = ctot ? atomicAdd(&cs->n_new[set][j], ctot) : 0u;
       __syncthreads();
-      pos += s_base;
-#pragma unroll
-      for (int u = 0; u < E; ++u)
-        if (clm >> u & 1u) J.slot_of[pos++] = slot[u];
+      if (warp == 0) {
+        const uint32_t vq = lane < NW ? s_wq[lane] : 0u, vc = lane < NW ? s_wc[lane] : 0u;
+        const uint32_t iq = warp_incl_scan(vq), ic = warp_incl_scan(vc);
+        const uint32_t tq = __shfl_sync(0xffffffffu, iq, 31), tc = __shfl_sync(0xffffffffu, ic, 31);
+        uint32_t bq = 0, bc = 0;
+        if (lane == 0) {
+          bq = tq ? atomicAdd(&cs->n_pass[set][j], tq) : 0u;
+          bc = tc ? atomicAdd(&cs->n_new[set][j], tc) : 0u;
+        }
+        bq = __shfl_sync(0xffffffffu, bq, 0);
+        bc = __shfl_sync(0xffffffffu, bc, 0);
+        if (lane < NW) {
+          s_wq[lane] = bq + iq - vq;
+          s_wc[lane] = bc + ic - vc;
+        }
+      }
+      __syncthreads();
+      const uint32_t pb = s_wq[warp];
+      uint32_t eb = s_wc[warp];
+      for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        uint32_t sl = kNone, rk = 0;
+        if (i < qn) {
+          sl = q_key[i];
+          rk = q_rank[i];
+          J.tmp_row[pb + i] = q_row[i];
+          J.tmp_slot[pb + i] = sl;
+          J.newslots[pb + i] = rk;
+        }
+        const bool first = sl != kNone && rk == 0;
+        const uint32_t fm = __ballot_sync(0xffffffffu, first);
+        if (first) J.slot_of[eb + __popc(fm & lanemask_lt())] = sl;
+        eb += __popc(fm);
+      }
+      __syncthreads();  // the queues are reused by the next sweep
     }
   }
   if (__syncthreads_or(dup) && tid == 0) cs->dup[set] = 1u;
   if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
   // Every key has exactly one row: D places the rows and there is no E.
   const bool scatter = ld_acquire_gpu(&cs->dup[set]) != 0;
-  if (tid < uint32_t(nj)) s_nn[tid] = ld_acquire_gpu(&cs->n_new[set][tid]);
+  if (tid < uint32_t(nj)) {
+    s_np[tid] = ld_acquire_gpu(&cs->n_pass[set][tid]);
+    s_nn[tid] = ld_acquire_gpu(&cs->n_new[set][tid]);
+  }
   __syncthreads();
 
   // The level's bookkeeping (block 0, while the others assign entries;
   // nothing in D or E reads it).  The table's dirty slots are the listed
-  // ones from here on.  The entries' fill cursors stay where D leaves them:
+  // ones from here on; the Bloom filter is used when it has at least four
+  // bits per key.  The entries' fill cursors stay where D leaves them:
   // forcing the next level resets the cursors of the parents it regroups.
   if (blockIdx.x == 0 && tid < uint32_t(nj)) {
     const int j = tid;
@@ -1297,6 +1267,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
                1ull << fj.jobs[j].x);
       atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)np);
+      L.filter_on = J.filter && uint64_t(nn) * 4 <= uint64_t(J.filter_words) * 32;
       L.n_rows = J.src;
       L.n_tmp = np;
       L.n_new = nn;
@@ -1306,7 +1277,6 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       L.n_req = 0;
       L.n_in = 0;
       L.n_listed = nn;
-      L.last_slots = s_mask[j] + 2;
       L.ht_state = kHtListed;
     }
   }

@@ -205,6 +205,70 @@ def test_chooser_gain(fj, ctx):
     model.free()
 
 
+def test_chooser_time_gain(fj, ctx):
+    """Trained on device times of queries composed from a pool of relations
+    of 300K-3M rows, the chooser (order and cover policy together) runs
+    held-out queries -- generated apart, with their own relations -- in less
+    time than the plain converted binary plan and than the fewest-keys
+    cover, with identical results.  Each candidate is timed as the best of
+    three executions from scratch between CUDA events."""
+    import torch
+    pool = G.chooser_pool(16, 300_000, 3_000_000, seed=23)
+    dpool = {r["name"]: ctx.relation([torch.from_numpy(c).cuda() for c in r["cols"]])
+             for r in pool}
+    rng = np.random.default_rng(1)
+    xs, ys = [], []
+    for q in range(120):
+        atoms, _ = G.pool_query(pool, q, base_seed=3000)
+        dev = [{"rel": dpool[a["rel"]["name"]], "vars": a["vars"], "rel_cols": a["rel_cols"]}
+               for a in atoms]
+        rows = C.samples(fj, ctx, dev, C.training_candidates([a["vars"] for a in atoms], 6, rng),
+                         label="time")
+        assert len({c for _, _, c in rows}) == 1
+        xs += [f for f, _, _ in rows]
+        ys += [t for _, t, _ in rows]
+    for r in dpool.values():
+        r.release()
+    model, losses = C.fit(fj, ctx, np.stack(xs), np.array(ys))
+    assert losses[-1] < 0.6 * losses[0]
+    stream = torch.cuda.current_stream()
+
+    def best_ms(prep):
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            prep.reset()
+            e0.record(stream)
+            prep.execute_async()
+            e1.record(stream)
+            prep.result()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    tot = {"plain": 0.0, "fewest": 0.0, "learned": 0.0}
+    for q in range(2100, 2108):
+        atoms, _ = G.chooser_query(q, 300_000, 3_000_000)
+        dev, _ = device_atoms(fj, ctx, atoms)
+        declared = fj.binary_to_free_plan(dev, list(range(len(atoms))), factor=True)
+        plan, pol, _ = fj.choose_plan(ctx, dev, model)
+        preps = {"plain": fj.Prepared(ctx, dev, declared, out_mode="count"),
+                 "fewest": fj.Prepared(ctx, dev, declared, out_mode="count", cover="fewest"),
+                 "learned": fj.Prepared(ctx, dev, plan, out_mode="count", cover=pol)}
+        counts = {k: p.execute().count for k, p in preps.items()}
+        assert len(set(counts.values())) == 1  # bit-exact whatever it picks
+        for k, p in preps.items():
+            tot[k] += best_ms(p)
+            p.free()
+        for a in dev:
+            a["rel"].release()
+    print("ms summed over held-out queries:", {k: round(v, 2) for k, v in tot.items()})
+    assert tot["learned"] < tot["plain"]
+    assert tot["learned"] <= tot["fewest"]
+    model.free()
+
+
 def test_degree_histogram_kernel_matches_oracle(fj, ctx):
     import torch
 
