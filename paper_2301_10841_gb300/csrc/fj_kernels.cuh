@@ -236,11 +236,6 @@ __device__ __forceinline__ uint32_t* slot_e(uint4* ht, int wide, uint32_t s) {
 __device__ __forceinline__ uint32_t* slot_cnt(uint4* ht, int wide, uint32_t s) {
   return wide ? &ht[2 * size_t(s) + 1].y : &ht[s].w;
 }
-// The root build keeps the row that claimed a slot here until the slot's
-// entry is assigned (a narrow slot's entry field; a wide slot's spare word).
-__device__ __forceinline__ uint32_t* slot_row(uint4* ht, int wide, uint32_t s) {
-  return wide ? &ht[2 * size_t(s) + 1].z : &ht[s].z;
-}
 // Empty a slot.
 __device__ __forceinline__ void slot_clear(uint4* ht, int wide, uint32_t s) {
   if (wide) {
@@ -750,7 +745,7 @@ __global__ void k_force_reset_req(ForceJobs fj) {
 constexpr int kRootThreads = 512;
 constexpr int kRootRows = 12;  // rows per thread per sweep of C
 // Dynamic shared memory of k_force_roots: per warp a queue of 32 x kRootRows
-// (row, key or slot, rank) triples.
+// (row, key then slot, rank) entries.
 constexpr size_t kRootSmem = size_t(kRootThreads) * kRootRows * 3 * sizeof(uint32_t);
 
 struct RootsState {        // zero at the start of each execution (k_reset)
@@ -943,10 +938,11 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   const int nj = fj.n_jobs;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   // Per warp, C's queue of the rows of a sweep that pass the selection:
-  // QW rows, QW keys (then their slots), QW ranks.
+  // QW rows, QW one-column keys (then the rows' slots), QW ranks.
   extern __shared__ __align__(16) uint32_t s_queue[];
   uint32_t* q_row = s_queue + size_t(warp) * 3 * QW;
   uint32_t* q_key = q_row + QW;
+  uint32_t* q_slot = q_key;
   uint32_t* q_rank = q_key + QW;
   __shared__ RootJob s_job[FJ_MAX_ATOMS];
   __shared__ uint32_t s_off[FJ_MAX_ATOMS + 1];
@@ -1169,7 +1165,6 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
           if (slot[u] != kNone) {
             rank = atomicAdd(slot_cnt(J.ht, J.wide, slot[u]), 1u);
             if (rank == 0) {
-              *slot_row(J.ht, J.wide, slot[u]) = rw[u];
               ++n_first;
             } else {
               dup = true;
@@ -1177,7 +1172,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
                 atomicMin(reinterpret_cast<int*>(&J.sbegin[slot[u]]), __ldg(J.tcol + rw[u]));
             }
           }
-          q_key[i] = slot[u];
+          q_slot[i] = slot[u];
           q_rank[i] = rank;
         }
       }
@@ -1210,17 +1205,42 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       uint32_t eb = s_wc[warp];
       for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
         const uint32_t i = i0 + lane;
-        uint32_t sl = kNone, rk = 0;
+        uint32_t sl = kNone, rk = 0, row = 0;
         if (i < qn) {
-          sl = q_key[i];
+          sl = q_slot[i];
           rk = q_rank[i];
-          J.tmp_row[pb + i] = q_row[i];
+          row = q_row[i];
+          J.tmp_row[pb + i] = row;
           J.tmp_slot[pb + i] = sl;
           J.newslots[pb + i] = rk;
         }
         const bool first = sl != kNone && rk == 0;
         const uint32_t fm = __ballot_sync(0xffffffffu, first);
-        if (first) J.slot_of[eb + __popc(fm & lanemask_lt())] = sl;
+        if (first) {
+          // The entry, as if its key had only this row (D corrects the
+          // ranges when some key repeats): list position er, offset er.
+          const uint32_t er = eb + __popc(fm & lanemask_lt()), e = J.base_e + er;
+          J.slot_of[er] = sl;
+          *slot_e(J.ht, J.wide, sl) = e;
+          uint64_t kw = 0;  // wide entries keep only the parent (the root: 0)
+          if (!J.wide) {
+            if (sl == mask + 1) {
+              kw = kEmptyKey;
+            } else {  // the key word from its slot
+              const uint4 v = J.ht[sl];
+              kw = (uint64_t(v.y) << 32) | v.x;
+            }
+          }
+          J.key[e] = kw;
+          J.count[e] = 1;
+          J.begin[e] = er;
+          J.fill[e] = J.ident ? er : row;  // a row read from perm: D places it
+          if (J.ident) J.perm[er] = row;
+          if (J.cstate) J.cstate[e] = kUnforced;
+          if (J.cnkeys) J.cnkeys[e] = 0;
+          if (J.cfirst) J.cfirst[e] = 0;
+          if (J.tmin) J.tmin[e] = __ldg(J.tcol + row);
+        }
         eb += __popc(fm);
       }
       __syncthreads();  // the queues are reused by the next sweep
@@ -1228,7 +1248,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   }
   if (__syncthreads_or(dup) && tid == 0) cs->dup[set] = 1u;
   if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
-  // Every key has exactly one row: D places the rows and there is no E.
+  // Every key has exactly one row: no E.
   const bool scatter = ld_acquire_gpu(&cs->dup[set]) != 0;
   if (tid < uint32_t(nj)) {
     s_np[tid] = ld_acquire_gpu(&cs->n_pass[set][tid]);
@@ -1236,11 +1256,11 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   }
   __syncthreads();
 
-  // The level's bookkeeping (block 0, while the others assign entries;
-  // nothing in D or E reads it).  The table's dirty slots are the listed
-  // ones from here on; the Bloom filter is used when it has at least four
-  // bits per key.  The entries' fill cursors stay where D leaves them:
-  // forcing the next level resets the cursors of the parents it regroups.
+  // The level's bookkeeping (block 0, while the others go on; nothing in
+  // D or E reads it).  The table's dirty slots are the listed ones from
+  // here on; the Bloom filter is used when it has at least four bits per
+  // key.  The entries' fill cursors stay at their first offsets: forcing
+  // the next level resets the cursors of the parents it regroups.
   if (blockIdx.x == 0 && tid < uint32_t(nj)) {
     const int j = tid;
     const RootJob& J = s_job[j];
@@ -1262,7 +1282,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
         P.begin[0] = 0;
         P.count[0] = np;
       }
-      if (!scatter) *J.pfill = np;  // D places the rows without the cursor
+      if (!scatter) *J.pfill = np;  // the rows were placed without the cursor
       atomicAdd(&res->ctr[FJ_CTR_ROOTS_BUILT], 1ull);
       atomicOr(reinterpret_cast<unsigned long long*>(&res->ctr[FJ_CTR_ATOM_BUILT_MASK]),
                1ull << fj.jobs[j].x);
@@ -1281,12 +1301,18 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     }
   }
 
-  // D: the listed slots become the root's entries (entry i of the level is
-  // list position i), each with its range of offsets inside the root's
-  // range, ED consecutive entries per thread.  When every key has one row
-  // (no scatter) entry i's range is offset i and the entry places its row
-  // (the row that claimed the slot); otherwise the ranges follow a block
-  // scan of the counts, one advance of the root's fill cursor per sweep.
+  // The entries C wrote are final when every key has one row and every
+  // job's rows are the base table's.
+  bool fix = scatter;
+  for (int j = 0; j < nj; ++j) fix |= s_job[j].act && !s_job[j].ident;
+  if (!fix) return;
+
+  // D: each entry's range inside the root's range, ED consecutive entries
+  // per thread: when some key repeats, its count from the slot and its
+  // first offset from a block scan of the counts (one advance of the root's
+  // fill cursor per sweep), and a tail level's MIN folds the slot's running
+  // MIN in; otherwise offset = list position, and a row that came from perm
+  // (kept in the entry's fill cursor by C) is placed here.
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_nn[j] : 0u; });
   block_range(s_off[nj], lo, hi);
   for (int j = 0; j < nj; ++j) {
@@ -1296,37 +1322,26 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     const uint32_t r1 = a1 - s_off[j];
     constexpr int ED = E;  // entries per thread per sweep
     for (uint32_t r = a0 - s_off[j]; r < r1; r += ED * NT) {
-      uint32_t sl[ED], cnt[ED], crow[ED], sum = 0;
-      uint64_t kw[ED];
-      int32_t smin[ED];  // a tail level: the MIN of the rows after the first
+      uint32_t sl[ED], cnt[ED], prow[ED], sum = 0;
+      int32_t smin[ED];
       const uint32_t i0 = r + tid * ED;
 #pragma unroll
       for (int u = 0; u < ED; ++u) sl[u] = i0 + u < r1 ? J.slot_of[i0 + u] : kNone;
 #pragma unroll
       for (int u = 0; u < ED; ++u) {
+        const uint32_t e = J.base_e + i0 + u;
         cnt[u] = 0;
-        crow[u] = 0;
-        kw[u] = 0;
+        prow[u] = 0;
         smin[u] = 0;
         if (sl[u] == kNone) continue;
-        if (J.tmin) smin[u] = int32_t(J.sbegin[sl[u]]);
-        if (J.wide) {
-          const uint4 v = J.ht[2 * size_t(sl[u]) + 1];
-          cnt[u] = v.y;
-          crow[u] = v.z;
-          kw[u] = 0;  // wide entries keep only the parent (the root: 0)
-        } else {
-          const uint4 v = J.ht[sl[u]];
-          cnt[u] = v.w;
-          crow[u] = v.z;
-          kw[u] = sl[u] == s_mask[j] + 1 ? kEmptyKey : ((uint64_t(v.y) << 32) | v.x);
+        cnt[u] = 1;
+        if (scatter) {
+          cnt[u] = *slot_cnt(J.ht, J.wide, sl[u]);
+          if (J.tmin) smin[u] = min(J.tmin[e], int32_t(J.sbegin[sl[u]]));
+        } else if (!J.ident) {
+          prow[u] = J.fill[e];
         }
         sum += cnt[u];
-      }
-      if (J.tmin) {  // and the first row's value
-#pragma unroll
-        for (int u = 0; u < ED; ++u)
-          if (sl[u] != kNone) smin[u] = min(smin[u], __ldg(J.tcol + crow[u]));
       }
       uint32_t b = i0;  // the root's range starts at 0
       if (scatter) {
@@ -1340,17 +1355,16 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       for (int u = 0; u < ED; ++u) {
         if (sl[u] == kNone) continue;
         const uint32_t e = J.base_e + i0 + u;
-        *slot_e(J.ht, J.wide, sl[u]) = e;
-        if (J.tmin) J.tmin[e] = smin[u];
-        if (cnt[u] == 1) J.perm[b] = crow[u];
-        J.sbegin[sl[u]] = b;
-        J.key[e] = kw[u];
-        J.count[e] = cnt[u];
-        J.begin[e] = b;
-        J.fill[e] = b;
-        if (J.cstate) J.cstate[e] = kUnforced;
-        if (J.cnkeys) J.cnkeys[e] = 0;
-        if (J.cfirst) J.cfirst[e] = 0;
+        if (scatter) {
+          J.count[e] = cnt[u];
+          J.begin[e] = b;
+          J.fill[e] = b;
+          J.sbegin[sl[u]] = b;
+          if (J.tmin) J.tmin[e] = smin[u];
+        } else {  // a row from perm, placed at its entry's offset
+          J.perm[b] = prow[u];
+          J.fill[e] = b;
+        }
         b += cnt[u];
       }
       if (scatter) __syncthreads();
