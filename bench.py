@@ -164,6 +164,22 @@ def probe_phase_bytes(fact, dims, theta):
     return total, survivors
 
 
+def build_bytes(dims, theta):
+    """Compulsory bytes of the root build of the star plan's four dimension
+    roots: 4 B per row for each column read (key and selection attribute),
+    and per passing row (every key has one row) 16 B for clearing the slot
+    the previous build used, 12 B of staging (row, slot, rank) and 48 B of
+    entry (slot entry word, key word, count, first offset, fill cursor,
+    child state, child first, child key count, slot list, the row's offset,
+    the tail MIN)."""
+    total = 0
+    for d in dims:
+        key, attr = d["cols"]
+        total += 8 * len(key)
+        total += (16 + 12 + 48) * int((attr < theta).sum())
+    return total
+
+
 def source_hash():
     h = hashlib.sha256()
     for f in ("fj_kernels.cuh", "fj_exec.cuh", "fj_scan.cuh", "fj_internal.h"):
@@ -352,7 +368,7 @@ def run_fj(args, rank, world):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    times, expand_ns, expand_n, kernels = [], 0, 0, 0
+    times, expand_ns, expand_n, kernels, build_ns = [], 0, 0, 0, 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -367,6 +383,7 @@ def run_fj(args, rank, world):
         times.append(e0.elapsed_time(e1))
         expand_ns += res.counters["expand_ns"]
         expand_n += res.counters["expand_launches"]
+        build_ns += res.counters["build_ns"]
         kernels += res.counters["kernels"]
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -423,6 +440,20 @@ def run_fj(args, rank, world):
                 "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
                 "traffic": profiled_traffic(khash), "algorithmic_bytes": alg,
                 "launch_us": launch_s * 1e6, "kernel_source": khash}
+    # The root build (k_force_roots, one launch per step) against the same
+    # peak, and the whole step: every algorithmic byte of the step over the
+    # step's time.
+    b_alg = build_bytes(dims, THETA)
+    b_s = build_ns / max(1, args.steps) / 1e9
+    b_ach = b_alg / b_s / 1e9 if b_s > 0 else None
+    roofline_build = {"bound": "hbm", "kernel": "k_force_roots (the four dimension roots)",
+                      "achieved": b_ach, "peak": peak, "unit": "GB/s",
+                      "frac": b_ach / peak if b_ach else None, "peak_kind": peak_kind,
+                      "algorithmic_bytes": b_alg, "launch_us": b_s * 1e6}
+    step_s = statistics.mean(times) / 1000
+    roofline_step = {"bound": "hbm", "algorithmic_bytes": alg + b_alg,
+                     "achieved": (alg + b_alg) / step_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": (alg + b_alg) / step_s / 1e9 / peak, "step_us": step_s * 1e6}
     cpu, parity = None, None
     if not args.no_cpu_baseline and world == 1:
         cpu, exact = cpu_baseline_leg(fact, dims)
@@ -435,7 +466,8 @@ def run_fj(args, rank, world):
             "data": "synthetic", "config": workload_config(args.n_fact),
             "result": {"count": expect[0], "mins": expect[1], "survivors": survivors},
             "parity": parity,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "roofline_build": roofline_build,
+            "roofline_step": roofline_step, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "counters": res.counters,
             "gpu_launches": kernels, "impl": "fj"}
     print(json.dumps(line), flush=True)
@@ -890,6 +922,76 @@ def run_chooser(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# Sixth workload (--workload rmat-4cycle): the 4-cycle count on the full-size
+# R-MAT graph (config 3's cyclic query), one execution of minutes, checked
+# against the oracle's 2-path count stored in tests/golden/rmat_counts.json
+# (written by tests/golden/make_rmat_counts.py --full-size, oracle only).
+# ---------------------------------------------------------------------------
+
+RMAT4_METRIC = "tuples/sec (in+out), R-MAT 4-cycle count, Generic Join plan, fewest-keys cover"
+
+
+def run_rmat4(args, rank, world):
+    import torch
+
+    from paper_2301_10841_gb300 import fj
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scale = args.rmat_scale or RMAT_SCALE
+    n_edges = 16 << scale
+    e = G.rmat(scale, n_edges, seed=3)
+    ctx = fj.Context(local)
+    rel = ctx.relation([torch.from_numpy(c).to(dev) for c in e["cols"]], "E")
+    q = G.four_cycle_query(e)
+    atoms = [{"rel": rel, "vars": a["vars"], "rel_cols": a["rel_cols"]} for a in q]
+    plan = fj.generic_join_plan(atoms, [0, 1, 2, 3])
+    prep = fj.Prepared(ctx, atoms, plan, out_mode="count", cover="fewest")
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prep.execute_async()
+    e1.record(stream)
+    res = prep.result()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    want = None
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "rmat_counts.json")) as f:
+            gold = json.load(f)
+        recs = gold["graphs"] + ([gold["full_size"]] if "full_size" in gold else [])
+        for r in recs:
+            if r["scale"] == scale and "four_cycles_two_paths" in r:
+                want = r["four_cycles_two_paths"]
+    except (OSError, KeyError, ValueError):
+        pass
+    if want is not None and want != res.count:
+        raise SystemExit(f"4-cycle count {res.count} differs from the oracle's {want}")
+    if rank != 0:
+        return
+    line = {"metric": RMAT4_METRIC, "value": (4 * n_edges + res.count) / (ms / 1000),
+            "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": f"R-MAT scale {scale} (2^{scale} vertices, {n_edges} edges "
+                                   "drawn, a,b,c = 0.57,0.19,0.19, seed 3), Q_4(w,x,y,z) :- "
+                                   "E(w,x),E(x,y),E(y,z),E(z,w), COUNT(*)",
+                       "plan": "Generic Join plan of the order w,x,y,z, fewest-keys cover",
+                       "timing": "one execution from scratch between CUDA events (it takes "
+                                 "minutes at full size: no warm-up and no repeats)"},
+            "result": {"count": res.count},
+            "parity": {"exact": want is not None, "oracle_two_paths": want},
+            "counters": res.counters, "clocks": clk, "roofline": None, "cpu_baseline": None,
+            "e2e": None, "gpu_launches": res.counters["kernels"], "impl": "fj"}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # Fifth workload (--workload ablation): the paper's COLT and vectorization
 # ablations (Section 5.3) and its Generic Join baseline (Section 5.1), on the
 # same GPU.  Tries: COLT (lazy), simple lazy trie (every root built eagerly)
@@ -928,6 +1030,7 @@ def _time_prepared(prep, flush, stream, steps, warmup):
 
 
 def run_ablation(args, rank, world):
+    args.rmat_scale = args.rmat_scale or 18
     import torch
 
     from paper_2301_10841_gb300 import fj
@@ -1018,8 +1121,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="star",
-                    choices=["star", "rmat-triangle", "batched", "chooser", "ablation"])
-    ap.add_argument("--rmat-scale", type=int, default=18)
+                    choices=["star", "rmat-triangle", "rmat-4cycle", "batched", "chooser",
+                             "ablation"])
+    ap.add_argument("--rmat-scale", type=int, default=None,
+                    help="R-MAT scale of the ablation (default 18) and 4-cycle (default 20) "
+                         "workloads")
     ap.add_argument("--train-queries", type=int, default=10_000)
     ap.add_argument("--train-min-rows", type=int, default=2_000)
     ap.add_argument("--train-max-rows", type=int, default=20_000)
@@ -1047,6 +1153,8 @@ def main():
             run_reference(args, rank, world)
         elif args.workload == "rmat-triangle":
             run_rmat(args, rank, world)
+        elif args.workload == "rmat-4cycle":
+            run_rmat4(args, rank, world)
         elif args.workload == "batched":
             run_batched(args, rank, world)
         elif args.workload == "chooser":

@@ -32,6 +32,30 @@ def trace_power(a, k):
     return int(round(t))
 
 
+def four_cycles_two_paths(src, dst, n, block=16384):
+    """Bag count of the 4-cycle query E(w,x),E(x,y),E(y,z),E(z,w) as
+    sum over (w, y) of P2[w, y] * P2[y, w], where P2 = A A counts the
+    2-paths from w to y (exact int64 sparse products; a 4-cycle is a
+    2-path w -> y followed by a 2-path y -> w).  Equal to trace(A^4) but
+    needs only the nonzeros of A^2, so it reaches graphs whose dense
+    adjacency matrix does not fit.  The w's are taken `block` at a time:
+    rows W of P2 are A[W] A, and the entries P2[y, w] for w in W are the
+    columns W of P2, A A[:, W]."""
+    import scipy.sparse as sp
+    a = sp.csr_matrix((np.ones(len(src), dtype=np.int64),
+                       (np.asarray(src, dtype=np.int64), np.asarray(dst, dtype=np.int64))),
+                      shape=(n, n))
+    a.sum_duplicates()
+    ac = a.tocsc()
+    total = 0
+    for w0 in range(0, n, block):
+        w1 = min(n, w0 + block)
+        rows = (a[w0:w1] @ a).tocsr()           # P2[w, y], w in W
+        cols = (a @ ac[:, w0:w1]).T.tocsr()     # P2[y, w] as [w, y], w in W
+        total += int(rows.multiply(cols).sum())
+    return total
+
+
 def complete_digraph_cycles(n, k):
     """trace((J - I)^k) for the complete directed graph on n vertices without
     self-loops: the eigenvalues of J - I are n - 1 (once) and -1 (n - 1 times),

@@ -525,6 +525,7 @@ class Prepared:
         self.ctx = ctx
         self.min_vars = list(min_vars or [])
         self.out_mode = out_mode
+        self.batch_size, self.load_factor = batch_size, load_factor
         self._head = list(head) if head is not None else None
         self._atoms_vars = [list(a["vars"]) for a in atoms]
         # The library borrows the relations' columns: keep them alive.
@@ -638,11 +639,13 @@ class Batch:
 
 
 def autotune(ctx, atoms, plan, out_mode="count", min_vars=None, cover="static",
-             batch_sizes=(256, 1024, 4096, 8192), load_factors=(0.25, 0.5), reps=2):
+             batch_sizes=(256, 1024, 4096, 8192), load_factors=(0.25, 0.5, 0.7), reps=2,
+             times=None):
     """Pick the cover-batch size and hash-level load factor with the shortest
     execution (device time between CUDA events, best of ``reps`` runs from
     scratch) and return ``(prepared, (batch_size, load_factor), ms)``; the
-    other candidates are freed.  Results do not depend on the choice."""
+    other candidates are freed.  Results do not depend on the choice.  When
+    ``times`` is a dict it receives every candidate's time."""
     import torch
     best = None
     stream = torch.cuda.current_stream()
@@ -661,6 +664,8 @@ def autotune(ctx, atoms, plan, out_mode="count", min_vars=None, cover="static",
                 p.result()
                 ms = e0.elapsed_time(e1)
                 t = ms if t is None else min(t, ms)
+            if times is not None:
+                times[(bs, lf)] = t
             if best is None or t < best[2]:
                 if best is not None:
                     best[0].free()

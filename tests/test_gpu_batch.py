@@ -72,3 +72,25 @@ def test_prepared_keeps_its_relations(fj, ctx):
     assert (r.count, r.mins) == want
     del junk
 
+
+
+def test_autotuner_picks_the_fastest_candidate(fj, ctx):
+    """The autotuner times every (cover-batch size, load factor) candidate
+    -- {256, 1024, 4096, 8192} x {0.25, 0.5, 0.7} -- and keeps the one with
+    the shortest time, configured as chosen; whatever it picks gives the
+    oracle's COUNT and MINs."""
+    for q in (0, 1, 5):
+        atoms, order, mins = G.batch_query(q, max_rows=200_000)
+        want = oracle.binary_join(atoms, order=order, min_vars=mins)[:2]
+        dev, _ = device_atoms(fj, ctx, atoms)
+        plan = fj.binary_to_free_plan(dev, order, factor=True)
+        times = {}
+        p, cfg, ms = fj.autotune(ctx, dev, plan, out_mode="count_min", min_vars=mins,
+                                 times=times)
+        assert set(times) == {(b, l) for b in (256, 1024, 4096, 8192) for l in (0.25, 0.5, 0.7)}
+        assert ms == min(times.values()) and times[cfg] == ms
+        assert (p.batch_size, p.load_factor) == cfg
+        p.reset()
+        r = p.execute()
+        assert (r.count, r.mins) == tuple(want)
+        p.free()

@@ -270,3 +270,21 @@ def test_pkfk_direct_catches_a_wrong_key():
     key = key[::-1].copy()  # keys still unique, rows now point elsewhere
     bad[1]["cols"] = [key] + list(bad[1]["cols"][1:])
     assert closed.pkfk_direct(bad, mins) != base
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_four_cycles_from_two_paths_equal_trace_of_a4(seed):
+    """The 2-path form (sum of P2[w,y] P2[y,w], sparse integer products) --
+    the oracle used for 4-cycles where enumeration is too slow -- against
+    trace(A^4) by dense matmul, multiplicities and self-loops included, and
+    against the complete digraph's closed form."""
+    e = G.uniform_digraph(80, 900, seed)
+    src = np.concatenate([e["cols"][0], e["cols"][0][:60], np.arange(5)])
+    dst = np.concatenate([e["cols"][1], e["cols"][1][:60], np.arange(5)])
+    a = closed.adjacency(src, dst, 80)
+    want = closed.trace_power(a, 4)
+    assert closed.four_cycles_two_paths(src, dst, 80) == want
+    assert closed.four_cycles_two_paths(src, dst, 80, block=7) == want  # rows in blocks
+    c = G.complete_digraph(9)
+    assert closed.four_cycles_two_paths(c["cols"][0], c["cols"][1], 9) == \
+        closed.complete_digraph_cycles(9, 4)
