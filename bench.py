@@ -815,10 +815,20 @@ def run_chooser(args, rank, world):
     t_train = time.perf_counter() - t_train
 
     # Held-out queries: the plain converted binary plan, the same plan with
-    # the fewest-keys cover, and the chooser's plan and policy.
-    policies = {"plain": [], "fewest": [], "learned": []}
-    in_tuples = 0
+    # the fewest-keys cover, and the chooser's plan and policy.  One query at
+    # a time (its three prepared plans, then freed: the large ones do not
+    # all fit at once); a step is one pass over every query, so each
+    # policy's time per step is the sum over queries of its mean time per
+    # execution (from scratch, L2 flushed before each, CUDA events).
+    names = ("plain", "fewest", "learned")
+    in_tuples, out_tuples = 0, 0
     choices = []
+    flush = L2Flush(dev)
+    stream = torch.cuda.current_stream()
+    ms = {k: 0.0 for k in names}
+    per_query = {k: [] for k in names}
+    clocks = ClockSampler(local)
+    clocks.start()
     for q in range(2000, 2000 + args.n_queries):
         atoms, kind = G.chooser_query(q, args.min_rows, args.max_rows)
         d = device(atoms)
@@ -826,51 +836,16 @@ def run_chooser(args, rank, world):
         declared = fj.binary_to_free_plan(d, list(range(len(atoms))), factor=True)
         plan, pol, order = fj.choose_plan(ctx, d, model)
         choices.append({"kind": kind, "order": order, "cover": pol})
-        policies["plain"].append(fj.Prepared(ctx, d, declared, out_mode="count"))
-        policies["fewest"].append(fj.Prepared(ctx, d, declared, out_mode="count", cover="fewest"))
-        policies["learned"].append(fj.Prepared(ctx, d, plan, out_mode="count", cover=pol))
-    flush = L2Flush(dev)
-    stream = torch.cuda.current_stream()
-
-    def run(preps):
-        out = []
-        for p in preps:
-            p.reset()
-            out.append(p.execute().count)
-        return out
-
-    expect = run(policies["plain"])
-    for name in ("fewest", "learned"):
-        if run(policies[name]) != expect:
-            raise SystemExit(f"{name} results differ from the plain plan's")
-    out_tuples = sum(expect)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms = {}
-    for name, preps in policies.items():
-        for _ in range(args.warmup):
-            run(preps)
-        times = []
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            got = run(preps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if got != expect:
-                raise SystemExit("result changed between steps")
-            times.append(e0.elapsed_time(e1))
-        ms[name] = sum(times) / len(times)
-    clk = clocks.stop()
-    # Each query alone (best of three, L2 flushed before each), per policy.
-    per_query = {name: [] for name in policies}
-    for name, preps in policies.items():
-        for p in preps:
-            best = None
-            for _ in range(3):
+        preps = {"plain": fj.Prepared(ctx, d, declared, out_mode="count"),
+                 "fewest": fj.Prepared(ctx, d, declared, out_mode="count", cover="fewest"),
+                 "learned": fj.Prepared(ctx, d, plan, out_mode="count", cover=pol)}
+        counts = {k: p.execute().count for k, p in preps.items()}
+        if len(set(counts.values())) != 1:
+            raise SystemExit(f"query {q}: results differ between policies: {counts}")
+        out_tuples += counts["plain"]
+        for k, p in preps.items():
+            times = []
+            for i in range(args.warmup + args.steps):
                 flush.zero_()
                 torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -879,11 +854,18 @@ def run_chooser(args, rank, world):
                 p.reset()
                 p.execute_async()
                 e1.record(stream)
-                p.result()
+                r = p.result()
                 torch.cuda.synchronize()
-                t = e0.elapsed_time(e1)
-                best = t if best is None else min(best, t)
-            per_query[name].append(round(best, 3))
+                if r.count != counts[k]:
+                    raise SystemExit("result changed between steps")
+                if i >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+            ms[k] += sum(times) / len(times)
+            per_query[k].append(round(min(times), 3))
+            p.free()
+        for a in d:
+            a["rel"].release()
+    clk = clocks.stop()
     if rank != 0:
         return
     tot = in_tuples + out_tuples

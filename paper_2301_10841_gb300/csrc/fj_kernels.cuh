@@ -1021,17 +1021,33 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     const int j = job_at(s_off, nj, x);
     reinterpret_cast<uint4*>(s_job[j].filter)[x - s_off[j]] = make_uint4(0u, 0u, 0u, 0u);
   }
+  // One contiguous part of the slots per block (equal parts), two per
+  // thread at a time with their list loads in flight together.
   jobs_prefix(nj, s_off, [&](int j) {
     const RootJob& J = s_job[j];
     if (!J.act) return 0u;
     return J.state == kHtListed ? J.n_listed : J.ht_cap_max + 1;
   });
-  for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
-    const int j = job_at(s_off, nj, x);
-    const RootJob& J = s_job[j];
-    const uint32_t sl = J.state == kHtListed ? J.slot_of[x - s_off[j]] : x - s_off[j];
-    slot_clear(J.ht, J.wide, sl);
-    if (J.tmin) J.sbegin[sl] = uint32_t(INT32_MAX);
+  block_range(s_off[nj], lo, hi);
+  for (uint32_t x0 = lo + tid; x0 < hi; x0 += 2 * NT) {
+    uint32_t sl[2];
+    int jj[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint32_t x = x0 + u * NT;
+      jj[u] = -1;
+      if (x >= hi) continue;
+      jj[u] = job_at(s_off, nj, x);
+      const RootJob& J = s_job[jj[u]];
+      sl[u] = J.state == kHtListed ? J.slot_of[x - s_off[jj[u]]] : x - s_off[jj[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (jj[u] < 0) continue;
+      const RootJob& J = s_job[jj[u]];
+      slot_clear(J.ht, J.wide, sl[u]);
+      if (J.tmin) J.sbegin[sl[u]] = uint32_t(INT32_MAX);
+    }
   }
   if (!grid_sync(cs, &res->status, spin, ++bar_target, test_timeout != 0)) return;
   // From here on a failed launch leaves the tables in an unknown state; a
@@ -1054,17 +1070,37 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   // order numbers the entries.  Per sweep one advance of the job's row and
   // key counters: the queues go to the staging arrays (for E) and the list
   // at those offsets.
+  // The work split: when every active job's rows fit in whole sweeps of
+  // the grid's blocks, each block takes at most one sweep of one job (no
+  // block waits on two chains); otherwise one contiguous part of all rows
+  // per block.
+  constexpr uint32_t SW = kRootRows * NT;  // rows per block sweep
+  jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? (s_job[j].src + SW - 1) / SW : 0u; });
+  const bool per_job = s_off[nj] <= gridDim.x;
+  int jsel = -1;
+  uint32_t jr0 = 0, jr1 = 0;
+  if (per_job && blockIdx.x < s_off[nj]) {
+    jsel = job_at(s_off, nj, blockIdx.x);
+    jr0 = (blockIdx.x - s_off[jsel]) * SW;
+    jr1 = min(s_job[jsel].src, jr0 + SW);
+  }
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_job[j].src : 0u; });
   block_range(s_off[nj], lo, hi);
   bool dup = false;  // some key of this block's rows has another row before it
   for (int j = 0; j < nj; ++j) {
-    const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
-    if (a0 >= a1) continue;
+    uint32_t r0 = jr0, r1 = jr1;  // this block's rows of job j
+    if (per_job) {
+      if (j != jsel) continue;
+    } else {
+      const uint32_t a0 = max(lo, s_off[j]), a1 = min(hi, s_off[j + 1]);
+      if (a0 >= a1) continue;
+      r0 = a0 - s_off[j];
+      r1 = a1 - s_off[j];
+    }
     const RootJob& J = s_job[j];
     const bool k1 = !J.wide && J.nk == 1;
     const uint32_t mask = s_mask[j];
-    const uint32_t r1 = a1 - s_off[j];
-    for (uint32_t r = a0 - s_off[j]; r < r1; r += kRootRows * NT) {
+    for (uint32_t r = r0; r < r1; r += SW) {
       uint32_t qn;
       {
         uint32_t row[kRootRows];
