@@ -274,7 +274,11 @@ fj_status fj_node_covers(const fj_query* query, const fj_plan* plan, int k,
 typedef struct {
   uint32_t batch_size;   /* cover tuples per vectorized batch (Fig. 13);
                             0 = default 1024; rounded to a supported size */
-  float load_factor;     /* COLT hash-level occupancy target; 0 = 0.25 */
+  float load_factor;     /* COLT hash-level occupancy target; 0 = 0.25.  Each
+                            level's table is allocated for all of its atom's
+                            rows at this load; a root level built in the
+                            one-launch root build spans the whole allocation
+                            (its occupancy is then at most this target) */
   int cover_policy;      /* FJ_COVER_* */
   int out_mode;          /* FJ_OUT_* */
   uint64_t list_limit;   /* MATERIALIZE: most rows to keep (0 = no limit) */
