@@ -122,3 +122,26 @@ def test_batched_workload_real_sizes(fj, ctx):
         assert (r.count, r.mins) == w
         p.free()
     torch.cuda.synchronize()
+
+
+def test_star_join_from_host_columns(fj, ctx):
+    """Relations copied from host memory (fj_load_relation_host, pinned and
+    pageable sources alike) give the direct-address star join's COUNT and
+    MINs."""
+    import torch
+    fact, dims = G.star_schema(n_fact=3_000_007, dims=(1000, 2500, 5000, 10_000), s=1.1, seed=5)
+    want = closed.star_join_direct(fact["cols"], [tuple(d["cols"]) for d in dims],
+                                   [G.STAR_THETA] * 4)
+    for pinned in (True, False):
+        def host(cols):
+            ts = [torch.from_numpy(np.ascontiguousarray(c)) for c in cols]
+            return [t.pin_memory() for t in ts] if pinned else ts
+        rels = {r["name"]: ctx.relation_host(host(r["cols"]), r["name"]) for r in [fact] + dims}
+        q = G.star_query(fact, dims, theta=G.STAR_THETA)
+        atoms = [{"rel": rels[a["rel"]["name"]], "vars": a["vars"], "preds": a["preds"]}
+                 for a in q]
+        plan = fj.binary_to_free_plan(atoms, [0, 1, 2, 3, 4], factor=True)
+        r = fj.execute(ctx, atoms, plan, out_mode="count_min", min_vars=[4, 5, 6, 7])
+        assert (r.count, r.mins) == want, pinned
+        for h in rels.values():
+            h.release()
