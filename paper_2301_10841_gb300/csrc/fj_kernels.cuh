@@ -1239,45 +1239,67 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       __syncthreads();
       const uint32_t pb = s_wq[warp];
       uint32_t eb = s_wc[warp];
-      for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
-        const uint32_t i = i0 + lane;
-        uint32_t sl = kNone, rk = 0, row = 0;
-        if (i < qn) {
-          sl = q_slot[i];
-          rk = q_rank[i];
-          row = q_row[i];
-          J.tmp_row[pb + i] = row;
-          J.tmp_slot[pb + i] = sl;
-          J.newslots[pb + i] = rk;
+      // Two queue entries per lane at a time, every global load (the key
+      // word from the slot, a tail level's value) issued before any store.
+      for (uint32_t i0 = 0; i0 < qn; i0 += 64) {
+        uint32_t sl[2], rk[2], row[2];
+        uint64_t kw[2];
+        int32_t tv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const uint32_t i = i0 + u * 32 + lane;
+          sl[u] = kNone;
+          rk[u] = 0;
+          row[u] = 0;
+          if (i < qn) {
+            sl[u] = q_slot[i];
+            rk[u] = q_rank[i];
+            row[u] = q_row[i];
+          }
         }
-        const bool first = sl != kNone && rk == 0;
-        const uint32_t fm = __ballot_sync(0xffffffffu, first);
-        if (first) {
-          // The entry, as if its key had only this row (D corrects the
-          // ranges when some key repeats): list position er, offset er.
-          const uint32_t er = eb + __popc(fm & lanemask_lt()), e = J.base_e + er;
-          J.slot_of[er] = sl;
-          *slot_e(J.ht, J.wide, sl) = e;
-          uint64_t kw = 0;  // wide entries keep only the parent (the root: 0)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          kw[u] = 0;  // wide entries keep only the parent (the root: 0)
+          tv[u] = 0;
+          if (sl[u] == kNone || rk[u] != 0) continue;
           if (!J.wide) {
-            if (sl == mask + 1) {
-              kw = kEmptyKey;
+            if (sl[u] == mask + 1) {
+              kw[u] = kEmptyKey;
             } else {  // the key word from its slot
-              const uint4 v = J.ht[sl];
-              kw = (uint64_t(v.y) << 32) | v.x;
+              const uint4 v = J.ht[sl[u]];
+              kw[u] = (uint64_t(v.y) << 32) | v.x;
             }
           }
-          J.key[e] = kw;
-          J.count[e] = 1;
-          J.begin[e] = er;
-          J.fill[e] = J.ident ? er : row;  // a row read from perm: D places it
-          if (J.ident) J.perm[er] = row;
-          if (J.cstate) J.cstate[e] = kUnforced;
-          if (J.cnkeys) J.cnkeys[e] = 0;
-          if (J.cfirst) J.cfirst[e] = 0;
-          if (J.tmin) J.tmin[e] = __ldg(J.tcol + row);
+          if (J.tmin) tv[u] = __ldg(J.tcol + row[u]);
         }
-        eb += __popc(fm);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const uint32_t i = i0 + u * 32 + lane;
+          if (i < qn) {
+            J.tmp_row[pb + i] = row[u];
+            J.tmp_slot[pb + i] = sl[u];
+            J.newslots[pb + i] = rk[u];
+          }
+          const bool first = sl[u] != kNone && rk[u] == 0;
+          const uint32_t fm = __ballot_sync(0xffffffffu, first);
+          if (first) {
+            // The entry, as if its key had only this row (D corrects the
+            // ranges when some key repeats): list position er, offset er.
+            const uint32_t er = eb + __popc(fm & lanemask_lt()), e = J.base_e + er;
+            J.slot_of[er] = sl[u];
+            *slot_e(J.ht, J.wide, sl[u]) = e;
+            J.key[e] = kw[u];
+            J.count[e] = 1;
+            J.begin[e] = er;
+            J.fill[e] = J.ident ? er : row[u];  // a row read from perm: D places it
+            if (J.ident) J.perm[er] = row[u];
+            if (J.cstate) J.cstate[e] = kUnforced;
+            if (J.cnkeys) J.cnkeys[e] = 0;
+            if (J.cfirst) J.cfirst[e] = 0;
+            if (J.tmin) J.tmin[e] = tv[u];
+          }
+          eb += __popc(fm);
+        }
       }
       __syncthreads();  // the queues are reused by the next sweep
     }
