@@ -750,7 +750,7 @@ constexpr size_t kRootSmem = size_t(kRootThreads) * kRootRows * 3 * sizeof(uint3
 
 struct RootsState {        // zero at the start of each execution (k_reset)
   unsigned int bar_count;  // block arrivals at grid barriers this execution
-  unsigned int bar_gen;    // grid barriers completed this execution
+  unsigned int bar_gen;    // unused (kept for the layout k_reset zeroes)
   // Per job: rows passing, keys; per launch: some key has more than one
   // row.  Launches alternate between the two sets; a launch zeroes the set
   // the next launch uses.
@@ -768,36 +768,28 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
 }
 
 // Grid-wide barrier among all blocks of a cooperative launch.  The arrival
-// counter and the generation only grow (k_reset zeroes both at the start of
-// an execution, so between barriers count = generation x grid): the block
-// that completes barrier number `target` (generations since the execution
-// began, counted by the caller) publishes it with one release store, and the
-// others poll it with acquire loads -- the arrival's release and the poll's
-// acquire order the blocks' writes around the barrier.  Returns false (in
-// every thread of the block) when the wait ran out; `never` (the test of
-// the bounded wait) makes the barrier wait for an arrival that never comes.
+// counter only grows (k_reset zeroes it at the start of an execution): each
+// block adds one with a release reduction, and waits, polling with acquire
+// loads, until the count reaches `target` (the caller's count of arrivals
+// at the end of this barrier) -- the releases and the acquire order the
+// blocks' writes around the barrier, and nobody has to publish the barrier's
+// end.  Returns false (in every thread of the block) when the wait ran out;
+// `never` (the test of the bounded wait) makes the barrier wait for an
+// arrival that never comes.
 __device__ __forceinline__ bool grid_sync(RootsState* cs, uint32_t* status, uint32_t spin,
                                           uint32_t target, bool never = false) {
   const uint32_t limit = spin ? spin : kGridSpinLimit;
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    unsigned int old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;"
-                 : "=r"(old)
-                 : "l"(&cs->bar_count)
-                 : "memory");
-    if (!never && old == target * gridDim.x - 1) {
-      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&cs->bar_gen), "r"(target)
-                   : "memory");
-    } else {
-      uint32_t it = 0;
-      while (ld_acquire_gpu(&cs->bar_gen) < target) {
-        if (++it > limit) {
-          atomicOr(status, kStTimeout);
-          ok = 0;
-          break;
-        }
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&cs->bar_count) : "memory");
+    const uint32_t want = never ? target + 1 : target;
+    uint32_t it = 0;
+    while (ld_acquire_gpu(&cs->bar_count) < want) {
+      if (++it > limit) {
+        atomicOr(status, kStTimeout);
+        ok = 0;
+        break;
       }
     }
   }
@@ -951,9 +943,11 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   __shared__ uint32_t s_wq[NW], s_wc[NW];  // per warp: queued rows, new keys
   __shared__ uint32_t s_scan[33];
   __shared__ uint32_t s_base2;
-  // Grid barriers completed before this launch (an execution may launch the
-  // build more than once); only thread 0 takes part in the barriers.
-  uint32_t bar_target = tid == 0 ? ld_acquire_gpu(&cs->bar_gen) : 0u;
+  // Arrivals at grid barriers before this launch (an execution may launch
+  // the build more than once): whole barriers of the same grid -- a block of
+  // this launch may already have arrived at the first one, so round down.
+  // Only thread 0 takes part in the barriers.
+  uint32_t bar_target = tid == 0 ? ld_acquire_gpu(&cs->bar_count) / gridDim.x * gridDim.x : 0u;
   if (tid < uint32_t(nj)) {
     const int2 jb = fj.jobs[tid];
     const AtomDev& a = fj.atoms[jb.x];
@@ -1049,7 +1043,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
       if (J.tmin) J.sbegin[sl[u]] = uint32_t(INT32_MAX);
     }
   }
-  if (!grid_sync(cs, &res->status, spin, ++bar_target, test_timeout != 0)) return;
+  if (!grid_sync(cs, &res->status, spin, bar_target += gridDim.x, test_timeout != 0)) return;
   // From here on a failed launch leaves the tables in an unknown state; a
   // complete one lists the slots it used.
   if (blockIdx.x == 0 && tid < uint32_t(nj) && s_job[tid].act) {
@@ -1305,7 +1299,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     }
   }
   if (__syncthreads_or(dup) && tid == 0) cs->dup[set] = 1u;
-  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
+  if (!grid_sync(cs, &res->status, spin, bar_target += gridDim.x)) return;
   // Every key has exactly one row: no E.
   const bool scatter = ld_acquire_gpu(&cs->dup[set]) != 0;
   if (tid < uint32_t(nj)) {
@@ -1430,7 +1424,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   }
 
   if (!scatter) return;
-  if (!grid_sync(cs, &res->status, spin, ++bar_target)) return;
+  if (!grid_sync(cs, &res->status, spin, bar_target += gridDim.x)) return;
 
   // E: every passing row to its place in its entry's range (the entry's
   // first offset, kept per slot by D, plus the row's rank from C).
