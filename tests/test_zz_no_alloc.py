@@ -22,6 +22,15 @@ def _existing_count(fj, ctx, r, s):
     return fj.execute(ctx, atoms, plan, out_mode="count").count
 
 
+def _bag_count(r, s):
+    """The bag COUNT of R(x), S(x) from its definition: the sum over keys of
+    the product of the two multiplicities (numpy, independent of the GPU)."""
+    kr, cr = np.unique(r, return_counts=True)
+    ks, cs = np.unique(s, return_counts=True)
+    _, ir, is_ = np.intersect1d(kr, ks, assume_unique=True, return_indices=True)
+    return int(np.dot(cr[ir].astype(np.uint64), cs[is_].astype(np.uint64)))
+
+
 def test_noalloc_join_count_matches_execute_plan_twice(fj):
     import torch
     ctx = fj.Context(0)
@@ -35,6 +44,7 @@ def test_noalloc_join_count_matches_execute_plan_twice(fj):
     ]
     for r, s in cases:  # two calls in a row on the shared scratch
         want = _existing_count(fj, ctx, r, s)
+        assert want == _bag_count(r, s)
         out = torch.full((1,), -7, dtype=torch.int64, device="cuda")
         fj.join2_count_noalloc(torch.from_numpy(r).cuda(), torch.from_numpy(s).cuda(), out)
         torch.cuda.synchronize()
