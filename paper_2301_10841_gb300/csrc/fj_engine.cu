@@ -920,6 +920,8 @@ static void setup_scan(fj_prepared* P) {
     S.filter = Pd.filter;
     S.filter_words = Pd.filter_words;
     S.filter_on = Pd.filter_on;
+    S.bitmap = nullptr;  // set below for the first probe of a one-launch scan
+    S.exact = &P->d_atoms[N.sub[Pd.sub].atom].L[N.sub[Pd.sub].lvl + 1].exact;
     track |= Pd.last;
   }
   if (sc.n_probe > 0) {
@@ -963,6 +965,19 @@ static void setup_scan(fj_prepared* P) {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan_fused<kFuseR>, kFuseThreads,
                                                      kFuseSmem));
     P->fuse_blocks = P->ctx->n_sm * std::max(1, b);
+    // The first probe's root level (one key column) also gets an exact key
+    // bitmap, built with the level; only this probe reads one.
+    const SubDev& S0 = N.sub[N.probe[0].sub];
+    AtomDev& A0 = P->host_atoms[S0.atom];
+    LevelDev& L0 = A0.L[S0.lvl + 1];
+    if (!P->sc0.probe[0].last && S0.lvl == 0 && L0.filter && L0.nk == 1 && !L0.wide) {
+      if (!L0.bitmap) {
+        L0.bitmap = P->alloc<uint32_t>(L0.filter_words);
+        CK(cudaMemcpyAsync(&P->d_atoms[S0.atom], &A0, sizeof(AtomDev), cudaMemcpyHostToDevice,
+                           P->ctx->stream));
+      }
+      P->sc0.probe[0].bitmap = L0.bitmap;
+    }
   }
 }
 

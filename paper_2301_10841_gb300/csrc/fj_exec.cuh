@@ -993,6 +993,7 @@ __global__ void k_reset(AtomDev* atoms, int n_atoms, ResultDev* res, int do_atom
       L.mask = 0;
       L.n_in = 0;
       L.filter_on = 0;
+      L.exact = 0;
     }
   }
   if (a == 0 && threadIdx.x == 0) {

@@ -77,6 +77,13 @@ struct LevelDev {
   // keys for its size.
   uint32_t* filter = nullptr;
   uint32_t filter_words = 0;  // power of two
+  // Root levels keyed by one column: one bit per key value in
+  // [0, 32 filter_words), set by the root build next to the Bloom filter.
+  // When every key falls in that range (`exact`, set by the build) the
+  // bitmap answers membership exactly: the node-0 scan then needs no hash
+  // lookup for the rows it keeps and fetches their entries only for the
+  // final survivors.
+  uint32_t* bitmap = nullptr;
   // Wide levels (more than one key value below the root, or three values)
   // use 32-byte slots {parent, k0, k1, k2 | entry, count, -, -} claimed with
   // a 16-byte compare-and-swap; their entries keep only the parent in key[]
@@ -98,6 +105,7 @@ struct LevelDev {
   uint32_t pos_total;  // offsets placed by the current force
   uint32_t n_in;       // rows that reach this level's table (sizing)
   uint32_t filter_on;  // the filter is built and selective
+  uint32_t exact;      // the bitmap holds every key of the level
   uint32_t n_tmp;      // (row, slot) pairs staged by the current force
   // State of the table between executions (kept across resets):
   // kHtListed: empty except the slots slot_of[0, n_listed) (and, for a

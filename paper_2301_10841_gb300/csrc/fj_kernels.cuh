@@ -412,8 +412,9 @@ __global__ void k_force_prepare(ForceJobs fj) {
   uint32_t cap = 16;
   while (float(cap) < want && cap < L.ht_cap_max) cap <<= 1;
   L.mask = cap - 1;
-  // This build leaves no list of the slots it writes.
+  // This build leaves no list of the slots it writes, and no bitmap.
   L.ht_state = kHtUnknown;
+  L.exact = 0;
   // Keep the filter only with at least 4 bits per key.
   L.filter_on = L.filter && uint64_t(L.n_in) * 4 <= uint64_t(L.filter_words) * 32;
 }
@@ -757,6 +758,7 @@ struct RootsState {        // zero at the start of each execution (k_reset)
   unsigned int n_pass[2][FJ_MAX_ATOMS];
   unsigned int n_new[2][FJ_MAX_ATOMS];
   unsigned int dup[2];
+  unsigned int oor[2][FJ_MAX_ATOMS];  // per job: some key outside the bitmap's range
 };
 
 constexpr uint32_t kGridSpinLimit = 1u << 22;  // polls of a grid barrier (about a second)
@@ -828,6 +830,7 @@ __device__ __forceinline__ void block_range(uint32_t total, uint32_t& lo, uint32
 struct RootJob {
   uint4* ht;
   uint32_t* filter;
+  uint32_t* bitmap;  // exact key bitmap (one-column narrow levels) or null
   uint32_t filter_words;
   uint32_t ht_cap_max;
   const int32_t* kc[3];
@@ -956,6 +959,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
     RootJob& J = s_job[tid];
     J.ht = L.ht;
     J.filter = L.filter;
+    J.bitmap = L.bitmap;
     J.filter_words = L.filter_words;
     J.ht_cap_max = L.ht_cap_max;
     J.nk = L.nk;
@@ -1000,6 +1004,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   if (blockIdx.x == 0 && tid < uint32_t(FJ_MAX_ATOMS)) {
     cs->n_pass[set ^ 1][tid] = 0;
     cs->n_new[set ^ 1][tid] = 0;
+    cs->oor[set ^ 1][tid] = 0;
     if (tid == 0) cs->dup[set ^ 1] = 0;
   }
   __syncthreads();
@@ -1009,11 +1014,15 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   // the slots its previous build listed (and a tail level's running MINs
   // there back to INT32_MAX), or, when no build left a list, every slot.
   jobs_prefix(nj, s_off, [&](int j) {
-    return s_job[j].act && s_job[j].filter ? s_job[j].filter_words / 4 : 0u;
+    const RootJob& J = s_job[j];
+    return J.act && J.filter ? J.filter_words / 4 * (J.bitmap ? 2u : 1u) : 0u;
   });
   for (uint32_t x = blockIdx.x * NT + tid; x < s_off[nj]; x += gridDim.x * NT) {
     const int j = job_at(s_off, nj, x);
-    reinterpret_cast<uint4*>(s_job[j].filter)[x - s_off[j]] = make_uint4(0u, 0u, 0u, 0u);
+    const RootJob& J = s_job[j];
+    const uint32_t u = x - s_off[j], fq = J.filter_words / 4;
+    uint32_t* w = u < fq ? J.filter : J.bitmap;  // the filter's words, then the bitmap's
+    reinterpret_cast<uint4*>(w)[u < fq ? u : u - fq] = make_uint4(0u, 0u, 0u, 0u);
   }
   // One contiguous part of the slots per block (equal parts), two per
   // thread at a time with their list loads in flight together.
@@ -1081,6 +1090,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
   jobs_prefix(nj, s_off, [&](int j) { return s_job[j].act ? s_job[j].src : 0u; });
   block_range(s_off[nj], lo, hi);
   bool dup = false;  // some key of this block's rows has another row before it
+  bool oor = false;  // some key of this block's sweep falls outside its job's bitmap
   for (int j = 0; j < nj; ++j) {
     uint32_t r0 = jr0, r1 = jr1;  // this block's rows of job j
     if (per_job) {
@@ -1171,6 +1181,12 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
             if (cl && J.filter) {
               const uint32_t fh = filter_hash(kw[u]);
               atomicOr(&J.filter[fh & (J.filter_words - 1)], bloom_bits(fh));
+              if (J.bitmap) {
+                if (kw[u] < 32ull * J.filter_words)
+                  atomicOr(&J.bitmap[kw[u] >> 5], 1u << (kw[u] & 31u));
+                else
+                  oor = true;
+              }
             }
           }
         } else {
@@ -1206,6 +1222,8 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
           q_rank[i] = rank;
         }
       }
+      if (__syncthreads_or(oor) && tid == 0) atomicOr(&cs->oor[set][j], 1u);
+      oor = false;
       // Offsets of this sweep's rows and keys: one advance of each counter
       // per block.
       n_first = __reduce_add_sync(0xffffffffu, n_first);
@@ -1340,6 +1358,7 @@ __global__ void __launch_bounds__(kRootThreads, 2) k_force_roots(ForceJobs fj, R
                1ull << fj.jobs[j].x);
       atomicAdd(&res->ctr[FJ_CTR_ROWS_REGROUPED], (unsigned long long)np);
       L.filter_on = J.filter && uint64_t(nn) * 4 <= uint64_t(J.filter_words) * 32;
+      L.exact = J.bitmap && !ld_acquire_gpu(&cs->oor[set][j]);
       L.n_rows = J.src;
       L.n_tmp = np;
       L.n_new = nn;

@@ -32,6 +32,8 @@ struct ScanProbe {
   const uint32_t* filter;
   uint32_t filter_words;
   const uint32_t* filter_on;  // device-side
+  const uint32_t* bitmap;     // exact key bitmap of a one-column root level (or null)
+  const uint32_t* exact;      // device-side: the bitmap holds every key
 };
 
 // Survivor buffer: structure of arrays, device-side count.
@@ -705,6 +707,35 @@ __device__ __forceinline__ uint32_t filter_bits(const int32_t* kt, const int32_t
   return pass;
 }
 
+// Exact membership bits of one tile for lane `lane` (same row-to-bit map as
+// filter_bits): the key's bit in the level's key bitmap `bm` of `nbits`
+// bits (keys outside it are not in the level).
+template <uint32_t G, bool FULL>
+__device__ __forceinline__ uint32_t bitmap_bits(const int32_t* kt, const int32_t* kg,
+                                                uint32_t here, const uint32_t* bm, uint32_t nbits,
+                                                uint32_t lane) {
+  uint32_t pass = 0;
+#pragma unroll
+  for (uint32_t g = 0; g < G; ++g) {
+    const uint32_t j0 = g * 128 + 4 * lane;
+    uint32_t k[4];
+    if (FULL) {
+      int4 v = *reinterpret_cast<const int4*>(&kt[j0]);
+      k[0] = uint32_t(v.x);
+      k[1] = uint32_t(v.y);
+      k[2] = uint32_t(v.z);
+      k[3] = uint32_t(v.w);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) k[i] = j0 + i < here ? uint32_t(__ldg(kg + j0 + i)) : nbits;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (k[i] < nbits && (bm[k[i] >> 5] >> (k[i] & 31u) & 1u)) pass |= 1u << (4 * g + i);
+  }
+  return pass;
+}
+
 template <int R>
 __global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_constant__ NodeDev nd,
                                                             const __grid_constant__ ScanDev sc,
@@ -758,12 +789,18 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_con
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // The first probe's filter, when it is on, into shared memory by one bulk
-  // copy that lands while the warps start their first tiles.
-  const bool fon0 = P.filter && *P.filter_on;
-  if (tid == 0 && fon0) {
+  // copy that lands while the warps start their first tiles -- or, when the
+  // level's key bitmap holds every key (and the probe does not end its
+  // atom), the bitmap: membership is then exact, the rows that pass are the
+  // probe's hits, and their entries are looked up only for the final
+  // survivors.
+  const bool ex0 = P.bitmap && !P.last && sc.k1 && *P.exact;
+  const bool fon0 = !ex0 && P.filter && *P.filter_on;
+  const bool copy0 = ex0 || fon0;
+  if (tid == 0 && copy0) {
     mbar_init(&s_fbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    tma_load_1d(s_filt, P.filter, P.filter_words * 4, &s_fbar);
+    tma_load_1d(s_filt, ex0 ? P.bitmap : P.filter, P.filter_words * 4, &s_fbar);
   }
   __syncthreads();
   // Lane 0 is the warp's producer: its first NS full tiles now, then each
@@ -782,7 +819,7 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_con
   const int32_t* kc1c = sc.probe[1].kcol[2];
   unsigned long long c_probe = 0, c_hit = 0, my_count = 0, surv = 0;
   bool any = false, timed_out = false;
-  if (fon0 && !mbar_wait(&s_fbar, 0, spin)) timed_out = true;
+  if (copy0 && !mbar_wait(&s_fbar, 0, spin)) timed_out = true;
   uint32_t n_surv = 0;  // survivors in the warp's region (the same in every lane)
   uint32_t t = t0;
   for (; t < t1; ++t) {
@@ -793,6 +830,33 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_con
     if (__any_sync(0xffffffffu, timed_out)) break;
     const int32_t* kt = keys[st];
     const int32_t* kg = kcol + size_t(t) * T;
+    if (ex0) {
+      // Exact: the rows that pass go straight to the warp's region.
+      const uint32_t nbits = P.filter_words * 32;
+      const uint32_t pass = staged ? bitmap_bits<G, true>(kt, kg, here, s_filt, nbits, lane)
+                                   : bitmap_bits<G, false>(kt, kg, here, s_filt, nbits, lane);
+      if (lane == 0) c_probe += here;
+      const uint32_t np = __popc(pass);
+      const uint32_t incl = warp_incl_scan(np);
+      uint32_t pos = region + n_surv + incl - np;
+      const uint32_t rbase = uint32_t(begin + size_t(t) * T);
+      for (uint32_t m = pass; m; m &= m - 1) {
+        const uint32_t bt = __ffs(m) - 1;
+        const uint32_t row = rbase + (bt >> 2) * 128 + 4 * lane + (bt & 3);
+        out.row[pos] = row;
+        if (out.mult) out.mult[pos] = 1u;
+        ++pos;
+        // The second probe gathers this row's key later: its sector into L2.
+        if (nk1 > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(kc1a + row));
+        if (nk1 > 1) asm volatile("prefetch.global.L2 [%0];" ::"l"(kc1b + row));
+        if (nk1 > 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(kc1c + row));
+      }
+      n_surv += __shfl_sync(0xffffffffu, incl, 31);
+      __syncwarp();
+      if (lane == 0 && t + NS < t1 && (t + NS + 1) * T <= n_rows)
+        tma_load_1d(keys[st], kcol + size_t(t + NS) * T, T * 4, &bar[st]);
+      continue;
+    }
     const uint32_t pass = staged ? filter_bits<G, true>(kt, kg, here, filt, fw1, lane)
                                  : filter_bits<G, false>(kt, kg, here, filt, fw1, lane);
     if (lane == 0) c_probe += here;
@@ -851,7 +915,7 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_con
     // out too is flagged apart).
     if (lane == 0) {
       atomicOr(&res->status, kStTimeout);
-      if (fon0 && !mbar_wait(&s_fbar, 0, 64u * spin)) atomicOr(&res->status, kStDrainTimeout);
+      if (copy0 && !mbar_wait(&s_fbar, 0, 64u * spin)) atomicOr(&res->status, kStDrainTimeout);
       for (uint32_t u = t; u < t1 && u < t + NS; ++u)
         if ((u + 1) * T <= n_rows &&
             !mbar_wait(&bar[(u - t0) % NS], ((u - t0) / NS) & 1u, 64u * spin))
@@ -938,6 +1002,39 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_scan_fused(const __grid_con
       }
     }
     n_list = n_out;
+  }
+  // The first probe's entries when its bitmap was exact, for the final
+  // survivors only (their keys are in the level: every lookup hits).
+  if (ex0 && keep_h) {
+    for (uint32_t i0 = 0; i0 < n_list; i0 += uint32_t(R) * 32) {
+      uint32_t key[R], ix[R];
+      uint4 sl[R];
+      uint32_t lv = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = i0 + r * 32 + lane, pos = region + i;
+        key[r] = 0;
+        ix[r] = pos;
+        if (i < n_list) {
+          lv |= 1u << r;
+          key[r] = out.row[pos];
+          if (sc.n_probe > 1) ix[r] = out.src[pos];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lv >> r & 1u) key[r] = uint32_t(__ldg(P.kcol[0] + key[r]));
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lv >> r & 1u) sl[r] = __ldg(&P.ht[hash_root1(int32_t(key[r])) & mask]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        uint32_t e = 0, cnt = 0;
+        if ((lv >> r & 1u) &&
+            root1_resolve(P.ht, mask, key[r], hash_root1(int32_t(key[r])) & mask, sl[r], e, cnt))
+          out.h[0][ix[r]] = e;
+      }
+    }
   }
   // Epilogue over the final list.
   for (uint32_t i0 = 0; i0 < n_list; i0 += uint32_t(R) * 32) {
