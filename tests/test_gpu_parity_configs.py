@@ -145,3 +145,27 @@ def test_star_join_from_host_columns(fj, ctx):
         assert (r.count, r.mins) == want, pinned
         for h in rels.values():
             h.release()
+
+
+def test_star_join_first_probe_bitmap_and_its_fallback(fj, ctx):
+    """The first probe of the one-launch scan tests an exact key bitmap when
+    every key of its root level lies in the bitmap's range (D1's keys
+    0..39,999), and falls back to the Bloom filter and hash lookup when one
+    does not (the same keys times 7: up to 279,993, past the 262,144 bits);
+    both give the direct-address star join's COUNT and MINs, executed twice
+    on one prepared plan."""
+    fact, dims = G.star_schema(n_fact=500_000, dims=(40_000, 2500, 5000, 10_000), s=1.1, seed=9)
+    for scale in (1, 7):
+        f = dict(fact, cols=[fact["cols"][0] * scale] + list(fact["cols"][1:]))
+        d = [dict(dims[0], cols=[dims[0]["cols"][0] * scale, dims[0]["cols"][1]])] + dims[1:]
+        want = closed.star_join_direct(f["cols"], [tuple(x["cols"]) for x in d],
+                                       [G.STAR_THETA] * 4)
+        atoms = G.star_query(f, d, theta=G.STAR_THETA)
+        dev, _ = device_atoms(fj, ctx, atoms)
+        plan = fj.binary_to_free_plan(dev, list(range(5)), factor=True)
+        p = fj.Prepared(ctx, dev, plan, out_mode="count_min", min_vars=[4, 5, 6, 7])
+        for _ in range(2):
+            p.reset()
+            r = p.execute()
+            assert (r.count, r.mins) == want, scale
+        p.free()
